@@ -1,0 +1,279 @@
+"""CPU oracle of the TPC sector tracker — TEST INFRASTRUCTURE ONLY.
+
+Only ``tests/``, ``__graft_entry__.smoke()`` and the CPU-baseline leg of
+``bench.py`` may import this package.  The CUDA product path never routes
+through it.
+
+The tracker itself is plain C (``tracker.c``), compiled twice: ``precision=64``
+runs it in double, ``precision=32`` in float (the paper's GPU tracker works in
+float; its CPU twin is the parity target).  Every step follows Section 1 of the
+paper (neighbours finder, evolution, tracklets from one-to-one link chains,
+Kalman tracklet construction, tracklet selection) with the weight of Section 3.1,
+the sorting of Section 3.2 and the 30-cluster minimum of Section 5.  Readings of
+the points the paper leaves open are the defaults of ``Config``.
+
+Pinned by ``tests/test_oracle_*.py`` against closed forms, brute force, the
+generator's truth and hand-built cases.
+"""
+from __future__ import annotations
+
+import ctypes
+import dataclasses
+import os
+import subprocess
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_LIB_PATH = os.path.join(_HERE, "liboracle.so")
+_SOURCES = ["common.c", "tracker.c"]
+_lock = threading.Lock()
+_lib = None
+
+
+def build(force: bool = False) -> str:
+    """Compile liboracle.so with gcc (no floating-point contraction, OpenMP over sectors)."""
+    srcs = [os.path.join(_HERE, s) for s in _SOURCES] + [os.path.join(_HERE, h) for h in ("oracle.h", "oracle_internal.h")]
+    if not force and os.path.exists(_LIB_PATH):
+        newest = max(os.path.getmtime(s) for s in srcs)
+        if os.path.getmtime(_LIB_PATH) >= newest:
+            return _LIB_PATH
+    flags = ["-O2", "-fPIC", "-std=c11", "-ffp-contract=off", "-fno-fast-math", "-fopenmp", "-Wall"]
+    objs = []
+    jobs = [("common.c", [], "common.o"), ("tracker.c", [], "tracker_f64.o"),
+            ("tracker.c", ["-DORC_F32"], "tracker_f32.o")]
+    procs = []
+    for src, extra, obj in jobs:
+        out = os.path.join(_HERE, obj)
+        objs.append(out)
+        procs.append(subprocess.Popen(["gcc", *flags, *extra, "-c", os.path.join(_HERE, src), "-o", out]))
+    for p in procs:
+        if p.wait() != 0:
+            raise RuntimeError("oracle compilation failed")
+    tmp = _LIB_PATH + ".tmp%d" % os.getpid()
+    subprocess.check_call(["gcc", "-shared", "-fopenmp", *objs, "-o", tmp, "-lm"])
+    os.replace(tmp, _LIB_PATH)
+    for o in objs:
+        os.remove(o)
+    return _LIB_PATH
+
+
+class _Cfg(ctypes.Structure):
+    _fields_ = [
+        ("n_rows", ctypes.c_int), ("row_x", ctypes.POINTER(ctypes.c_double)),
+        ("tan_half", ctypes.c_double), ("bz", ctypes.c_double), ("n_sectors", ctypes.c_int),
+        ("sigma_y", ctypes.c_double), ("sigma_z", ctypes.c_double),
+        ("nb_ty", ctypes.c_double), ("nb_tz", ctypes.c_double), ("nb_gate", ctypes.c_double),
+        ("min_chain", ctypes.c_int), ("seed_cov", ctypes.c_double * 5),
+        ("win_nsigma", ctypes.c_double), ("chi2_max", ctypes.c_double), ("max_miss", ctypes.c_int),
+        ("edge_margin", ctypes.c_double), ("sin_max", ctypes.c_double),
+        ("alpha", ctypes.c_double), ("beta", ctypes.c_double), ("min_clusters", ctypes.c_int),
+        ("qpt_max", ctypes.c_double), ("bin_dy", ctypes.c_double), ("bin_dz", ctypes.c_double),
+        ("brute_force", ctypes.c_int), ("n_threads", ctypes.c_int),
+    ]
+
+
+INFO = ["n", "n_starts", "n_tracks", "n_track_hits", "n_rows", "visits", "candidates", "in_window",
+        "nb_candidates", "updates"]
+PTRS = ["up_raw", "dn_raw", "up", "dn", "starts", "tl_nhits", "tl_ndf", "tl_nup", "tl_hits",
+        "tl_par", "tl_cov", "tl_x", "tl_chi2", "tl_w", "owner", "tl_nowned", "tl_accept",
+        "trk_tracklet", "trk_first", "trk_nhits", "trk_hits"]
+
+
+def lib():
+    global _lib
+    with _lock:
+        if _lib is None:
+            build()
+            L = ctypes.CDLL(_LIB_PATH)
+            P = ctypes.c_void_p
+            for pre in ("f64", "f32"):
+                f = getattr(L, "orc_track_event_" + pre)
+                f.restype = P
+                f.argtypes = [ctypes.POINTER(_Cfg), P, P, P, P, ctypes.c_int64]
+                g = getattr(L, "orc_propagate_" + pre)
+                g.restype = ctypes.c_int
+                g.argtypes = [P, P, ctypes.c_double, ctypes.c_double, ctypes.c_double, ctypes.c_double]
+            L.orc_result_info.argtypes = [P, P]
+            L.orc_result_ptrs.argtypes = [P, P]
+            L.orc_result_free.argtypes = [P]
+            L.orc_seed_f64.restype = ctypes.c_int
+            L.orc_seed_f64.argtypes = [P, P, P, ctypes.c_double, ctypes.c_double, P]
+            L.orc_bin_row_f32.argtypes = [P, P, ctypes.c_int, ctypes.c_float, ctypes.c_float,
+                                          ctypes.c_float, ctypes.c_float, ctypes.c_int, ctypes.c_int,
+                                          P, P, P]
+            _lib = L
+    return _lib
+
+
+@dataclasses.dataclass
+class Config:
+    """Tracker constants.  alpha = 6 (Section 3.1) and min_clusters = 30 (Section 5)
+    are the paper's; the rest are readings of points it leaves open."""
+    row_x: np.ndarray
+    n_sectors: int = 36
+    bz: float = 0.5
+    tan_half: float = 0.17632698070846498
+    sigma_y: float = 0.08
+    sigma_z: float = 0.1
+    nb_ty: float = 1.0
+    nb_tz: float = 2.0
+    nb_gate: float = 9.0
+    min_chain: int = 3
+    seed_cov: tuple = (0.08 * 0.08, 0.1 * 0.1, 0.01, 0.01, 1.0)
+    win_nsigma: float = 3.0
+    chi2_max: float = 16.0
+    max_miss: int = 10
+    edge_margin: float = 2.0
+    sin_max: float = 0.99
+    alpha: float = 6.0
+    beta: float = 1.0
+    min_clusters: int = 30
+    qpt_max: float = 20.0
+    bin_dy: float = 2.0
+    bin_dz: float = 4.0
+    brute_force: bool = False
+    n_threads: int = 0
+
+    def _c(self):
+        rx = np.ascontiguousarray(self.row_x, dtype=np.float64)
+        c = _Cfg()
+        c.n_rows = rx.shape[0]
+        c.row_x = rx.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+        for f in ("tan_half", "bz", "sigma_y", "sigma_z", "nb_ty", "nb_tz", "nb_gate", "win_nsigma",
+                  "chi2_max", "edge_margin", "sin_max", "alpha", "beta", "qpt_max", "bin_dy", "bin_dz"):
+            setattr(c, f, float(getattr(self, f)))
+        for f in ("n_sectors", "min_chain", "max_miss", "min_clusters", "n_threads"):
+            setattr(c, f, int(getattr(self, f)))
+        c.brute_force = int(bool(self.brute_force))
+        for i in range(5):
+            c.seed_cov[i] = float(self.seed_cov[i])
+        return c, rx
+
+
+def config_for(geometry, **kw) -> Config:
+    """Config for an ``eventgen.Geometry``."""
+    return Config(row_x=np.asarray(geometry.row_x, dtype=np.float64), n_sectors=geometry.n_sectors,
+                  bz=geometry.bz, tan_half=geometry.tan_half, **kw)
+
+
+@dataclasses.dataclass
+class Result:
+    """Everything the oracle produced for one event (input cluster indices throughout)."""
+    info: dict
+    up_raw: np.ndarray
+    dn_raw: np.ndarray
+    up: np.ndarray
+    dn: np.ndarray
+    starts: np.ndarray
+    tl_nhits: np.ndarray
+    tl_ndf: np.ndarray
+    tl_nup: np.ndarray
+    tl_hits: np.ndarray          # [T, n_rows], entries [:nhits] outer to inner
+    tl_par: np.ndarray           # [T, 5]
+    tl_cov: np.ndarray           # [T, 15] lower triangle, row-major
+    tl_x: np.ndarray
+    tl_chi2: np.ndarray
+    tl_w: np.ndarray
+    owner: np.ndarray
+    tl_nowned: np.ndarray
+    tl_accept: np.ndarray
+    trk_tracklet: np.ndarray
+    trk_first: np.ndarray
+    trk_nhits: np.ndarray
+    trk_hits: np.ndarray
+
+    def track_hits(self, i: int) -> np.ndarray:
+        f = self.trk_first[i]
+        return self.trk_hits[f:f + self.trk_nhits[i]]
+
+    def tracklet_hits(self, t: int) -> np.ndarray:
+        return self.tl_hits[t, :self.tl_nhits[t]]
+
+
+def track_event(cfg: Config, y, z, row, counts, precision: int = 32) -> Result:
+    """Run the whole tracker on one event.  ``y, z`` may be float32 or float64."""
+    L = lib()
+    y = np.ascontiguousarray(y, dtype=np.float64)
+    z = np.ascontiguousarray(z, dtype=np.float64)
+    row = np.ascontiguousarray(row, dtype=np.uint8)
+    counts = np.ascontiguousarray(counts, dtype=np.int32)
+    n = y.shape[0]
+    if counts.shape[0] != cfg.n_sectors * len(cfg.row_x) or int(counts.sum()) != n:
+        raise ValueError("counts must have n_sectors*n_rows entries summing to the cluster count")
+    c, _keep = cfg._c()
+    fn = L.orc_track_event_f64 if precision == 64 else L.orc_track_event_f32
+    h = fn(ctypes.byref(c), y.ctypes.data, z.ctypes.data, row.ctypes.data, counts.ctypes.data, n)
+    try:
+        info = np.zeros(len(INFO), dtype=np.int64)
+        L.orc_result_info(h, info.ctypes.data)
+        ptrs = (ctypes.c_void_p * len(PTRS))()
+        L.orc_result_ptrs(h, ptrs)
+        d = dict(zip(INFO, (int(v) for v in info)))
+        N, T, M, H, nr = d["n"], d["n_starts"], d["n_tracks"], d["n_track_hits"], d["n_rows"]
+
+        def arr(name, ctype, count, dtype):
+            p = ptrs[PTRS.index(name)]
+            if count == 0 or not p:
+                return np.zeros(0, dtype=dtype)
+            buf = (ctype * count).from_address(p)
+            return np.frombuffer(buf, dtype=dtype, count=count).copy()
+
+        i32, f64 = ctypes.c_int32, ctypes.c_double
+        out = dict(
+            up_raw=arr("up_raw", i32, N, np.int32), dn_raw=arr("dn_raw", i32, N, np.int32),
+            up=arr("up", i32, N, np.int32), dn=arr("dn", i32, N, np.int32),
+            starts=arr("starts", i32, T, np.int32), tl_nhits=arr("tl_nhits", i32, T, np.int32),
+            tl_ndf=arr("tl_ndf", i32, T, np.int32), tl_nup=arr("tl_nup", i32, T, np.int32),
+            tl_hits=arr("tl_hits", i32, T * nr, np.int32).reshape(T, nr),
+            tl_par=arr("tl_par", f64, T * 5, np.float64).reshape(T, 5),
+            tl_cov=arr("tl_cov", f64, T * 15, np.float64).reshape(T, 15),
+            tl_x=arr("tl_x", f64, T, np.float64), tl_chi2=arr("tl_chi2", f64, T, np.float64),
+            tl_w=arr("tl_w", f64, T, np.float64), owner=arr("owner", i32, N, np.int32),
+            tl_nowned=arr("tl_nowned", i32, T, np.int32),
+            tl_accept=arr("tl_accept", ctypes.c_uint8, T, np.uint8),
+            trk_tracklet=arr("trk_tracklet", i32, M, np.int32),
+            trk_first=arr("trk_first", i32, M, np.int32), trk_nhits=arr("trk_nhits", i32, M, np.int32),
+            trk_hits=arr("trk_hits", i32, H, np.int32),
+        )
+    finally:
+        L.orc_result_free(h)
+    return Result(info=d, **out)
+
+
+def propagate(state, cov15, x0, x1, bz=0.5, sin_max=0.99, precision: int = 64):
+    """Transport a state (y, z, sinphi, tanl, q/pT) and its covariance from x0 to x1."""
+    L = lib()
+    s = np.array(state, dtype=np.float64)
+    c = np.array(cov15, dtype=np.float64)
+    fn = L.orc_propagate_f64 if precision == 64 else L.orc_propagate_f32
+    ok = fn(s.ctypes.data, c.ctypes.data, float(x0), float(x1), float(bz), float(sin_max))
+    return bool(ok), s, c
+
+
+def seed(x3, y3, z3, bz=0.5, sin_max=0.99):
+    """Seed state from the first, middle and last points of a chain (double precision)."""
+    L = lib()
+    x3 = np.ascontiguousarray(x3, dtype=np.float64)
+    y3 = np.ascontiguousarray(y3, dtype=np.float64)
+    z3 = np.ascontiguousarray(z3, dtype=np.float64)
+    st = np.zeros(5)
+    ok = L.orc_seed_f64(x3.ctypes.data, y3.ctypes.data, z3.ctypes.data, float(bz), float(sin_max), st.ctypes.data)
+    return bool(ok), st
+
+
+def bin_row(y, z, ymin, zmin, inv_dy, inv_dz, ny, nz):
+    """A1 for one row with given grid parameters: per-cluster cell, the stable
+    counting-sort permutation and the cell starts."""
+    L = lib()
+    y = np.ascontiguousarray(y, dtype=np.float64)
+    z = np.ascontiguousarray(z, dtype=np.float64)
+    n = y.shape[0]
+    cell = np.zeros(max(n, 1), dtype=np.int32)
+    perm = np.zeros(max(n, 1), dtype=np.int32)
+    cs = np.zeros(ny * nz + 1, dtype=np.int32)
+    L.orc_bin_row_f32(y.ctypes.data, z.ctypes.data, n, ctypes.c_float(ymin), ctypes.c_float(zmin),
+                      ctypes.c_float(inv_dy), ctypes.c_float(inv_dz), int(ny), int(nz),
+                      cell.ctypes.data, perm.ctypes.data, cs.ctypes.data)
+    return cell[:n], perm[:n], cs

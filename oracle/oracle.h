@@ -1,0 +1,115 @@
+/* CPU oracle of the TPC sector tracker (test infrastructure only).
+ *
+ * A plain, slow, sequential restatement of the sector tracker of
+ * Rohr et al., "ALICE HLT TPC Tracking of Pb-Pb Events on GPUs" (2012):
+ * neighbours finder, evolution, tracklets from chains of one-to-one links,
+ * Kalman tracklet construction and tracklet selection (Section 1), the cluster
+ * weight w = n (alpha - chi2/beta) (Section 3.1), track sorting (Section 3.2)
+ * and the 30-cluster minimum (Section 5).  Every point the paper leaves open is
+ * fixed by a parameter in orc_config; the readings are documented next to the
+ * code that applies them.
+ *
+ * It is compiled twice from tracker.c: once with `real` = double (suffix _f64)
+ * and once with `real` = float (suffix _f32).  Only the tests, the smoke check
+ * and the CPU-baseline leg of the benchmark may load it; the product path never
+ * does.  It shares no code with the CUDA library.
+ */
+#ifndef TPC_ORACLE_H
+#define TPC_ORACLE_H
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct {
+    /* geometry (Section 1: 2 x 18 sectors, 159 pad rows) */
+    int n_rows;
+    const double *row_x;      /* [n_rows] cm */
+    double tan_half;          /* tan(10 deg): sector half-opening */
+    double bz;                /* tesla */
+    int n_sectors;
+    /* measurement model */
+    double sigma_y, sigma_z;  /* cluster errors (cm) */
+    /* neighbours finder window and gate */
+    double nb_ty, nb_tz;      /* |dy| <= ty*dx, |dz| <= tz*dx */
+    double nb_gate;           /* accept score <= nb_gate * (1 + wd^2 + wu^2) */
+    /* start hits */
+    int min_chain;            /* clusters in a chain */
+    /* construction */
+    double seed_cov[5];       /* diagonal of the seed covariance */
+    double win_nsigma;        /* search window half-width in sigmas */
+    double chi2_max;          /* 2-dof gate on a cluster */
+    int max_miss;             /* consecutive rows without a cluster that end a pass */
+    double edge_margin;       /* stop when |y| > x*tan_half + margin */
+    double sin_max;           /* stop when |sin phi| >= sin_max */
+    /* selection */
+    double alpha, beta;       /* weight w = n * (alpha - (chi2/ndf)/beta) */
+    int min_clusters;         /* Section 5: 30 */
+    double qpt_max;           /* low-momentum cut |q/pT| <= qpt_max */
+    /* the oracle's own search grid (results do not depend on it) */
+    double bin_dy, bin_dz;
+    int brute_force;          /* 1: every search scans whole rows instead of grid bins */
+    int n_threads;            /* OpenMP threads over sectors (<=0: runtime default) */
+} orc_config;
+
+/* Result of one event.  Indices of clusters are input ("original") indices. */
+typedef struct orc_result orc_result;
+
+enum {
+    ORC_INFO_N = 0,           /* clusters */
+    ORC_INFO_N_STARTS,        /* tracklets (= start hits) */
+    ORC_INFO_N_TRACKS,
+    ORC_INFO_N_TRACK_HITS,
+    ORC_INFO_N_ROWS,
+    ORC_INFO_VISITS,          /* construction row visits (both passes) */
+    ORC_INFO_CANDIDATES,      /* construction clusters inside grid bin ranges */
+    ORC_INFO_IN_WINDOW,       /* construction clusters inside the search window */
+    ORC_INFO_NB_CANDIDATES,   /* neighbours finder clusters inside bin ranges (both rows) */
+    ORC_INFO_UPDATES,         /* construction Kalman updates (both passes) */
+    ORC_INFO_COUNT
+};
+
+enum {
+    ORC_PTR_UP_RAW = 0, ORC_PTR_DN_RAW, ORC_PTR_UP, ORC_PTR_DN,           /* int32 [N] */
+    ORC_PTR_STARTS,                                                      /* int32 [T] */
+    ORC_PTR_TL_NHITS, ORC_PTR_TL_NDF, ORC_PTR_TL_NUP,                    /* int32 [T] */
+    ORC_PTR_TL_HITS,                                                     /* int32 [T*n_rows], outer to inner */
+    ORC_PTR_TL_PAR, ORC_PTR_TL_COV, ORC_PTR_TL_X, ORC_PTR_TL_CHI2, ORC_PTR_TL_W, /* double */
+    ORC_PTR_OWNER,                                                       /* int32 [N] */
+    ORC_PTR_TL_NOWNED,                                                   /* int32 [T] */
+    ORC_PTR_TL_ACCEPT,                                                   /* uint8 [T] */
+    ORC_PTR_TRK_TRACKLET, ORC_PTR_TRK_FIRST, ORC_PTR_TRK_NHITS,          /* int32 [M] */
+    ORC_PTR_TRK_HITS,                                                    /* int32 [sum nhits], inner to outer */
+    ORC_PTR_COUNT
+};
+
+void orc_default_config(orc_config *cfg, const double *row_x, int n_rows, int n_sectors);
+
+orc_result *orc_track_event_f64(const orc_config *cfg, const double *y, const double *z,
+                                const uint8_t *row, const int32_t *counts, int64_t n);
+orc_result *orc_track_event_f32(const orc_config *cfg, const double *y, const double *z,
+                                const uint8_t *row, const int32_t *counts, int64_t n);
+void orc_result_info(const orc_result *r, int64_t *info /* [ORC_INFO_COUNT] */);
+void orc_result_ptrs(const orc_result *r, void **ptrs /* [ORC_PTR_COUNT] */);
+void orc_result_free(orc_result *r);
+
+/* Stage pieces exposed for pins. */
+/* A1: grid cell of every cluster of one row and the counting-sort permutation
+ * (stable in input order).  cell[i] for i < n; perm[j] = local index of the j-th
+ * cluster in cell order; cell_start[0..ny*nz]. */
+void orc_bin_row_f32(const double *y, const double *z, int n, float ymin, float zmin,
+                     float inv_dy, float inv_dz, int ny, int nz,
+                     int32_t *cell, int32_t *perm, int32_t *cell_start);
+/* Helix propagation of a state (y, z, sinphi, tanl, q/pT) from x0 to x1;
+ * returns 0 when |sin phi| reaches sin_max. */
+int orc_propagate_f64(double *state, double *cov15, double x0, double x1, double bz, double sin_max);
+int orc_propagate_f32(double *state, double *cov15, double x0, double x1, double bz, double sin_max);
+/* Seed state from three (x, y, z) points (first, middle, last of a chain). */
+int orc_seed_f64(const double *x3, const double *y3, const double *z3, double bz, double sin_max,
+                 double *state);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

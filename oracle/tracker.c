@@ -1,0 +1,764 @@
+/* CPU oracle of the TPC sector tracker: a plain, sequential restatement of the
+ * algorithm of Section 1 with the cluster weight of Section 3.1, the track
+ * sorting of Section 3.2 and the 30-cluster minimum of Section 5.
+ *
+ * Test infrastructure only.  This file is compiled twice: with ORC_F32 defined
+ * (`real` = float, functions suffixed _f32) and without (`real` = double, _f64).
+ * It must be built with floating-point contraction off (-ffp-contract=off) so
+ * that every expression is evaluated exactly as written.
+ *
+ * Sectors are independent in the sector tracker (Section 1); like the paper's
+ * CPU tracker (Section 4) the sectors are distributed over OpenMP threads.
+ * Inside a sector everything is sequential, in the order the paper lists the
+ * steps.
+ */
+#include <math.h>
+#include <stdlib.h>
+#include <string.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
+#include "oracle_internal.h"
+
+#ifdef ORC_F32
+typedef float real;
+#define SQRT sqrtf
+#define ASIN asinf
+#define FABS fabsf
+#define SFX(name) name##_f32
+#else
+typedef double real;
+#define SQRT sqrt
+#define ASIN asin
+#define FABS fabs
+#define SFX(name) name##_f64
+#endif
+
+#define MAXB 4096            /* cap on grid cells per axis (the last cell absorbs the rest) */
+/* Bin ranges are looked up for a window widened by this many cm, so that a
+ * cluster which passes the exact window test can never fall in a cell outside
+ * the enumerated range because of rounding. */
+#define BIN_SLACK ((real)1e-3)
+
+/* ----------------------------------------------------------------------------------------- */
+/* constants of one run, in working precision                                                 */
+/* ----------------------------------------------------------------------------------------- */
+typedef struct {
+    int nr;
+    real *X;                      /* row x */
+    real th, margin, smax;
+    real sy2, sz2, isy2, isz2;
+    real ty, tz, gate9;
+    real cov0[5];
+    real nsig, chi2max;
+    int max_miss, min_chain, min_clusters;
+    real alpha, beta, qptmax;
+    real kB;                      /* curvature per unit q/pT: -kappa * Bz */
+    real bdy, bdz;
+    int brute;
+} K;
+
+static void make_consts(K *k, const orc_config *c)
+{
+    k->nr = c->n_rows;
+    k->X = (real *)malloc(sizeof(real) * (size_t)c->n_rows);
+    for (int i = 0; i < c->n_rows; i++) k->X[i] = (real)c->row_x[i];
+    k->th = (real)c->tan_half;
+    k->margin = (real)c->edge_margin;
+    k->smax = (real)c->sin_max;
+    real sy = (real)c->sigma_y, sz = (real)c->sigma_z;
+    k->sy2 = sy * sy;
+    k->sz2 = sz * sz;
+    k->isy2 = (real)1 / k->sy2;
+    k->isz2 = (real)1 / k->sz2;
+    k->ty = (real)c->nb_ty;
+    k->tz = (real)c->nb_tz;
+    k->gate9 = (real)c->nb_gate;
+    for (int i = 0; i < 5; i++) k->cov0[i] = (real)c->seed_cov[i];
+    k->nsig = (real)c->win_nsigma;
+    k->chi2max = (real)c->chi2_max;
+    k->max_miss = c->max_miss;
+    k->min_chain = c->min_chain;
+    k->min_clusters = c->min_clusters;
+    k->alpha = (real)c->alpha;
+    k->beta = (real)c->beta;
+    k->qptmax = (real)c->qpt_max;
+    k->kB = (real)(-ORC_KAPPA * c->bz);
+    k->bdy = (real)c->bin_dy;
+    k->bdz = (real)c->bin_dz;
+    k->brute = c->brute_force;
+}
+
+/* ----------------------------------------------------------------------------------------- */
+/* A1: per-row y/z grid and counting sort (initialisation, Section 2)                         */
+/* ----------------------------------------------------------------------------------------- */
+
+/* Cell index along one axis; monotone non-decreasing in v. */
+static int cell1(real v, real vmin, real inv, int nb)
+{
+    real t = (v - vmin) * inv;
+    if (!(t >= (real)0)) return 0;
+    if (t >= (real)nb) return nb - 1;
+    return (int)t;
+}
+
+typedef struct {
+    int64_t off, n;               /* global index range of the row */
+    real ymin, zmin, idy, idz;
+    int ny, nz;
+    int32_t *cstart;              /* [ny*nz+1] */
+    int32_t *sorted;              /* [n] global indices in cell order */
+} Row;
+
+static void bin_row(Row *rw, const real *Y, const real *Zc, real dy, real dz)
+{
+    int64_t n = rw->n;
+    real ymin = 0, ymax = 0, zmin = 0, zmax = 0;
+    for (int64_t i = 0; i < n; i++) {
+        real y = Y[rw->off + i], z = Zc[rw->off + i];
+        if (i == 0 || y < ymin) ymin = y;
+        if (i == 0 || y > ymax) ymax = y;
+        if (i == 0 || z < zmin) zmin = z;
+        if (i == 0 || z > zmax) zmax = z;
+    }
+    int ny = (int)ceil((double)((ymax - ymin) / dy));
+    int nz = (int)ceil((double)((zmax - zmin) / dz));
+    if (ny < 1) ny = 1;
+    if (nz < 1) nz = 1;
+    if (ny > MAXB) ny = MAXB;
+    if (nz > MAXB) nz = MAXB;
+    rw->ymin = ymin;
+    rw->zmin = zmin;
+    rw->idy = (real)1 / dy;
+    rw->idz = (real)1 / dz;
+    rw->ny = ny;
+    rw->nz = nz;
+    int nc = ny * nz;
+    rw->cstart = (int32_t *)calloc((size_t)nc + 1, sizeof(int32_t));
+    rw->sorted = (int32_t *)malloc(sizeof(int32_t) * (size_t)(n > 0 ? n : 1));
+    int32_t *cell = (int32_t *)malloc(sizeof(int32_t) * (size_t)(n > 0 ? n : 1));
+    for (int64_t i = 0; i < n; i++) {
+        int iy = cell1(Y[rw->off + i], ymin, rw->idy, ny);
+        int iz = cell1(Zc[rw->off + i], zmin, rw->idz, nz);
+        cell[i] = iz * ny + iy;
+        rw->cstart[cell[i] + 1]++;
+    }
+    for (int c = 0; c < nc; c++) rw->cstart[c + 1] += rw->cstart[c];
+    int32_t *fill = (int32_t *)malloc(sizeof(int32_t) * (size_t)nc);
+    memcpy(fill, rw->cstart, sizeof(int32_t) * (size_t)nc);
+    for (int64_t i = 0; i < n; i++) rw->sorted[fill[cell[i]]++] = (int32_t)(rw->off + i);
+    free(fill);
+    free(cell);
+}
+
+/* Clusters of a row inside |y - yc| <= wy and |z - zc| <= wz (exact test), found
+ * through the grid or, in brute-force mode, by scanning the whole row.  Returns
+ * the count; *ncand receives the clusters looked at. */
+static int row_window(const Row *rw, const real *Y, const real *Zc, int brute, real yc, real zc,
+                      real wy, real wz, int32_t *out, int64_t *ncand)
+{
+    int cnt = 0;
+    if (rw->n == 0) return 0;
+    if (brute) {
+        for (int64_t i = 0; i < rw->n; i++) {
+            int64_t g = rw->off + i;
+            if (FABS(Y[g] - yc) <= wy && FABS(Zc[g] - zc) <= wz) out[cnt++] = (int32_t)g;
+        }
+        *ncand += rw->n;
+        return cnt;
+    }
+    int iy0 = cell1(yc - wy - BIN_SLACK, rw->ymin, rw->idy, rw->ny);
+    int iy1 = cell1(yc + wy + BIN_SLACK, rw->ymin, rw->idy, rw->ny);
+    int iz0 = cell1(zc - wz - BIN_SLACK, rw->zmin, rw->idz, rw->nz);
+    int iz1 = cell1(zc + wz + BIN_SLACK, rw->zmin, rw->idz, rw->nz);
+    for (int iz = iz0; iz <= iz1; iz++) {
+        int a = rw->cstart[iz * rw->ny + iy0], b = rw->cstart[iz * rw->ny + iy1 + 1];
+        *ncand += b - a;
+        for (int j = a; j < b; j++) {
+            int32_t g = rw->sorted[j];
+            if (FABS(Y[g] - yc) <= wy && FABS(Zc[g] - zc) <= wz) out[cnt++] = g;
+        }
+    }
+    return cnt;
+}
+
+/* ----------------------------------------------------------------------------------------- */
+/* Kalman filter pieces (tracklet construction, Section 1)                                    */
+/* State p = (y, z, sin phi, tan lambda, q/pT) at a plane x; C is the full 5x5 covariance.    */
+/* ----------------------------------------------------------------------------------------- */
+typedef struct {
+    real p[5];
+    real C[5][5];
+} KS;
+
+static void set_diag(KS *s, const real *d)
+{
+    memset(s->C, 0, sizeof s->C);
+    for (int i = 0; i < 5; i++) s->C[i][i] = d[i];
+}
+
+/* Exact helix transport from x0 to x1 (curvature kB*q/pT, sin phi linear in x,
+ * chord and arc length of the circle) and C <- F C F^T with F its Jacobian.
+ * Returns 0 if |sin phi| at x1 reaches smax. */
+static int propagate(KS *s, real x0, real x1, real kB, real smax)
+{
+    real dx = x1 - x0;
+    real cur = kB * s->p[4];
+    real s0 = s->p[2];
+    real s1 = s0 + cur * dx;
+    if (!(FABS(s1) < smax)) return 0;
+    real c0 = SQRT((real)1 - s0 * s0);
+    real c1 = SQRT((real)1 - s1 * s1);
+    real A = s0 + s1;
+    real B = c0 + c1;
+    real tq = A / B;                          /* slope of the chord */
+    real dy = dx * tq;
+    real L = SQRT(dx * dx + dy * dy);         /* chord, signed like dx */
+    if (dx < 0) L = -L;
+    real u = (cur * L) * (real)0.5;           /* sin of half the turning angle */
+    real ratio = (u != 0) ? ASIN(u) / u : (real)1;
+    real dS = L * ratio;                      /* arc length = 2 asin(C L / 2) / C */
+    real tl = s->p[3];
+    real dz = tl * dS;
+
+    real F[5][5];
+    memset(F, 0, sizeof F);
+    for (int i = 0; i < 5; i++) F[i][i] = 1;
+    real BB = B * B;
+    F[0][2] = dx * ((real)2 * B + A * (s0 / c0 + s1 / c1)) / BB;     /* d y1 / d sinphi0 */
+    F[0][4] = dx * (kB * dx) * (B + A * (s1 / c1)) / BB;             /* d y1 / d q/pT */
+    F[2][4] = kB * dx;                                               /* d sinphi1 / d q/pT */
+    real g = (L != 0) ? ((real)1 / SQRT((real)1 - u * u)) * (dy / L) : (real)0; /* dS/dL * dL/ddy */
+    F[1][2] = tl * (g * F[0][2]);                                    /* d z1 / d sinphi0 */
+    F[1][3] = dS;                                                    /* d z1 / d tanl */
+    F[1][4] = tl * (g * F[0][4] + (((cur * L) * (L * L)) / (real)12) * kB); /* d z1 / d q/pT */
+
+    s->p[0] = s->p[0] + dy;
+    s->p[1] = s->p[1] + dz;
+    s->p[2] = s1;
+
+    real FC[5][5], N[5][5];
+    for (int i = 0; i < 5; i++)
+        for (int j = 0; j < 5; j++) {
+            real a = 0;
+            for (int k = 0; k < 5; k++) a = a + F[i][k] * s->C[k][j];
+            FC[i][j] = a;
+        }
+    for (int i = 0; i < 5; i++)
+        for (int j = 0; j < 5; j++) {
+            real a = 0;
+            for (int k = 0; k < 5; k++) a = a + FC[i][k] * F[j][k];
+            N[i][j] = a;
+        }
+    for (int i = 0; i < 5; i++)
+        for (int j = 0; j <= i; j++) s->C[i][j] = s->C[j][i] = N[i][j];
+    return 1;
+}
+
+/* Inverse of the 2x2 residual covariance S = H C H^T + R, H selecting (y, z). */
+typedef struct {
+    real Si[2][2];
+} Gain;
+
+static void residual_cov_inv(const KS *s, const K *k, Gain *g)
+{
+    real S00 = s->C[0][0] + k->sy2, S01 = s->C[0][1], S10 = s->C[1][0], S11 = s->C[1][1] + k->sz2;
+    real det = S00 * S11 - S01 * S10;
+    real idet = (real)1 / det;
+    g->Si[0][0] = S11 * idet;
+    g->Si[0][1] = -S01 * idet;
+    g->Si[1][0] = -S10 * idet;
+    g->Si[1][1] = S00 * idet;
+}
+
+static real chi2_of(const Gain *g, real r0, real r1)
+{
+    real t0 = g->Si[0][0] * r0 + g->Si[0][1] * r1;
+    real t1 = g->Si[1][0] * r0 + g->Si[1][1] * r1;
+    return r0 * t0 + r1 * t1;
+}
+
+/* Kalman update with measurement (my, mz): K = C H^T S^-1, p += K r, C -= K H C. */
+static void kf_update(KS *s, const Gain *g, real my, real mz)
+{
+    real r0 = my - s->p[0], r1 = mz - s->p[1];
+    real Kg[5][2];
+    for (int i = 0; i < 5; i++)
+        for (int m = 0; m < 2; m++) {
+            real a = 0;
+            for (int j = 0; j < 2; j++) a = a + s->C[i][j] * g->Si[j][m];
+            Kg[i][m] = a;
+        }
+    for (int i = 0; i < 5; i++) s->p[i] = s->p[i] + (Kg[i][0] * r0 + Kg[i][1] * r1);
+    real N[5][5];
+    for (int i = 0; i < 5; i++)
+        for (int j = 0; j < 5; j++) {
+            real a = 0;
+            for (int m = 0; m < 2; m++) a = a + Kg[i][m] * s->C[m][j];
+            N[i][j] = s->C[i][j] - a;
+        }
+    for (int i = 0; i < 5; i++)
+        for (int j = 0; j <= i; j++) s->C[i][j] = s->C[j][i] = N[i][j];
+}
+
+/* Seed: the circle through the (x, y) projections of three points gives y, sin phi
+ * and the curvature at the first point; tan lambda is the z rise over the arc
+ * length from the first to the last point. */
+static int seed3(const real *x, const real *y, const real *z, real kB, real smax, real *p)
+{
+    real ax = x[1] - x[0], ay = y[1] - y[0];
+    real bx = x[2] - x[0], by = y[2] - y[0];
+    real cx = x[2] - x[1], cy = y[2] - y[1];
+    real la = SQRT(ax * ax + ay * ay);
+    real lb = SQRT(bx * bx + by * by);
+    real lc = SQRT(cx * cx + cy * cy);
+    real cross = ax * by - ay * bx;
+    real den = (la * lb) * lc;
+    if (!(den > 0)) return 0;
+    real C = ((real)2 * cross) / den;         /* signed curvature, > 0 turning left */
+    real sa = (C * lb) * (real)0.5;           /* sin of the angle between chord and tangent */
+    if (!(FABS(sa) < (real)1)) return 0;
+    real ca = SQRT((real)1 - sa * sa);
+    real sinphi = (by / lb) * ca - (bx / lb) * sa;
+    if (!(FABS(sinphi) < smax)) return 0;
+    real S02 = (sa != 0) ? lb * (ASIN(sa) / sa) : lb;
+    p[0] = y[0];
+    p[1] = z[0];
+    p[2] = sinphi;
+    p[3] = (z[2] - z[0]) / S02;
+    p[4] = (kB != 0) ? C / kB : (real)0;
+    return 1;
+}
+
+/* ----------------------------------------------------------------------------------------- */
+/* one sector                                                                                 */
+/* ----------------------------------------------------------------------------------------- */
+typedef struct {
+    Row *rows;
+    int64_t off, n;
+    int64_t nstarts;
+    int32_t *starts;
+    int64_t cnt[ORC_INFO_COUNT];
+    /* output tracks of this sector */
+    int64_t ntracks;
+    int32_t *tracks;              /* tracklet ids in canonical order */
+} Sector;
+
+static int cmp_i64pair(const void *a, const void *b)
+{
+    const int64_t *x = (const int64_t *)a, *y = (const int64_t *)b;
+    return (x[0] > y[0]) - (x[0] < y[0]);
+}
+
+/* A1 .. A4 for one sector. */
+static void sector_links(Sector *S, const K *k, const real *Y, const real *Zc, const uint8_t *rowv,
+                         orc_result *res, int32_t *buf_u, int32_t *buf_d)
+{
+    int nr = k->nr;
+    for (int r = 0; r < nr; r++) bin_row(&S->rows[r], Y, Zc, k->bdy, k->bdz);
+
+    /* A2 neighbours finder: for each cluster of row k the best pair (u in k+1, d in k-1)
+     * that forms a straight line with it (Section 1, "Neighbors finder"). */
+    for (int r = 1; r + 1 < nr; r++) {
+        const Row *rc = &S->rows[r], *ru = &S->rows[r + 1], *rd = &S->rows[r - 1];
+        if (rc->n == 0 || ru->n == 0 || rd->n == 0) continue;
+        real xk = k->X[r], xu = k->X[r + 1], xd = k->X[r - 1];
+        real dxu = xu - xk, dxd = xk - xd;
+        real wyu = k->ty * dxu, wzu = k->tz * dxu;
+        real wyd = k->ty * dxd, wzd = k->tz * dxd;
+        real w = dxd / (xu - xd);             /* weight of u in the interpolation at x_k */
+        real om = (real)1 - w;
+        real gate = k->gate9 * (((real)1 + om * om) + w * w);
+        for (int64_t i = 0; i < rc->n; i++) {
+            int64_t c = rc->off + i;
+            real yc = Y[c], zc = Zc[c];
+            int nu = row_window(ru, Y, Zc, k->brute, yc, zc, wyu, wzu, buf_u, &S->cnt[ORC_INFO_NB_CANDIDATES]);
+            int nd = row_window(rd, Y, Zc, k->brute, yc, zc, wyd, wzd, buf_d, &S->cnt[ORC_INFO_NB_CANDIDATES]);
+            int32_t bu = -1, bd = -1;
+            real best = 0;
+            for (int a = 0; a < nu; a++)
+                for (int b = 0; b < nd; b++) {
+                    int32_t u = buf_u[a], d = buf_d[b];
+                    real dy = (yc - Y[d]) - (Y[u] - Y[d]) * w;
+                    real dz = (zc - Zc[d]) - (Zc[u] - Zc[d]) * w;
+                    real sc = dy * dy * k->isy2 + dz * dz * k->isz2;
+                    int better = (bu < 0) || (sc < best) || (sc == best && (u < bu || (u == bu && d < bd)));
+                    if (better) {
+                        best = sc;
+                        bu = u;
+                        bd = d;
+                    }
+                }
+            if (bu >= 0 && best <= gate) {
+                res->up_raw[c] = bu;
+                res->dn_raw[c] = bd;
+            }
+        }
+    }
+    /* A3 evolution: keep only reciprocal links (Section 1, "Evolution step"). */
+    for (int64_t c = S->off; c < S->off + S->n; c++) {
+        int32_t u = res->up_raw[c], d = res->dn_raw[c];
+        res->up[c] = (u >= 0 && res->dn_raw[u] == c) ? u : -1;
+        res->dn[c] = (d >= 0 && res->up_raw[d] == c) ? d : -1;
+    }
+    /* A4 start hits: heads of chains of one-to-one links with >= min_chain clusters,
+     * in (row, input index) order. */
+    S->starts = (int32_t *)malloc(sizeof(int32_t) * (size_t)(S->n > 0 ? S->n : 1));
+    S->nstarts = 0;
+    for (int64_t c = S->off; c < S->off + S->n; c++) {
+        if (res->up[c] < 0 || res->dn[c] >= 0) continue;
+        int len = 1;
+        int32_t t = (int32_t)c;
+        while (res->up[t] >= 0) {
+            t = res->up[t];
+            len++;
+        }
+        if (len >= k->min_chain) S->starts[S->nstarts++] = (int32_t)c;
+    }
+    (void)rowv;
+}
+
+/* Best cluster of row r for state s: minimum chi2, ties to the lower input index. */
+static int32_t search_row(Sector *S, const K *k, const real *Y, const real *Zc, const KS *s, int r,
+                          const Gain *g, real *chi2_out, int32_t *buf)
+{
+    const Row *rw = &S->rows[r];
+    real wy = k->nsig * SQRT(s->C[0][0] + k->sy2);
+    real wz = k->nsig * SQRT(s->C[1][1] + k->sz2);
+    int nc = row_window(rw, Y, Zc, k->brute, s->p[0], s->p[1], wy, wz, buf, &S->cnt[ORC_INFO_CANDIDATES]);
+    S->cnt[ORC_INFO_IN_WINDOW] += nc;
+    S->cnt[ORC_INFO_VISITS]++;
+    int32_t best = -1;
+    real bc = 0;
+    for (int i = 0; i < nc; i++) {
+        int32_t c = buf[i];
+        real x2 = chi2_of(g, Y[c] - s->p[0], Zc[c] - s->p[1]);
+        if (best < 0 || x2 < bc || (x2 == bc && c < best)) {
+            best = c;
+            bc = x2;
+        }
+    }
+    *chi2_out = bc;
+    return best;
+}
+
+/* A5 tracklet construction for the tracklet starting at cluster c0 (Section 1,
+ * "Tracklet construction"): seed from the chain, fit outwards while searching each
+ * row, then refit inwards from the outermost cluster with a fresh covariance. */
+static void construct(Sector *S, const K *k, const real *Y, const real *Zc, const uint8_t *rowv,
+                      orc_result *res, int64_t t, int32_t c0, int32_t *buf, int32_t *chain)
+{
+    int nr = k->nr;
+    int L = 0;
+    for (int32_t c = c0; c >= 0; c = res->up[c]) chain[L++] = c;
+    int m = (L - 1) / 2;
+    int32_t c3[3] = {chain[0], chain[m], chain[L - 1]};
+    real x3[3], y3[3], z3[3];
+    for (int i = 0; i < 3; i++) {
+        x3[i] = k->X[rowv[c3[i]]];
+        y3[i] = Y[c3[i]];
+        z3[i] = Zc[c3[i]];
+    }
+    int32_t *hits = res->tl_hits + (size_t)t * (size_t)nr;
+    res->tl_nhits[t] = 0;
+    res->tl_ndf[t] = -5;
+    res->tl_nup[t] = 0;
+    res->tl_w[t] = -INFINITY;
+    KS st;
+    if (!seed3(x3, y3, z3, k->kB, k->smax, st.p)) return;
+    set_diag(&st, k->cov0);
+    Gain g;
+    real chi2;
+
+    /* outward pass */
+    int r0 = rowv[c0];
+    real x = k->X[r0];
+    KS last = st;
+    real xlast = x;
+    int rlast = -1, miss = 0, nup = 0;
+    for (int r = r0; r < nr; r++) {
+        real xr = k->X[r];
+        if (r != r0) {
+            if (!propagate(&st, x, xr, k->kB, k->smax)) break;
+            x = xr;
+        }
+        if (FABS(st.p[0]) > xr * k->th + k->margin) break;
+        residual_cov_inv(&st, k, &g);
+        int32_t b = search_row(S, k, Y, Zc, &st, r, &g, &chi2, buf);
+        if (b >= 0 && chi2 <= k->chi2max) {
+            kf_update(&st, &g, Y[b], Zc[b]);
+            S->cnt[ORC_INFO_UPDATES]++;
+            nup++;
+            rlast = r;
+            last = st;
+            xlast = x;
+            miss = 0;
+        } else if (++miss >= k->max_miss) {
+            break;
+        }
+    }
+    res->tl_nup[t] = nup;
+    if (rlast < 0) return;
+
+    /* inward pass from the outermost cluster, covariance reset to the seed's */
+    st = last;
+    set_diag(&st, k->cov0);
+    x = xlast;
+    miss = 0;
+    int n = 0;
+    real chi2sum = 0;
+    KS inner = st;
+    real xin = x;
+    for (int r = rlast; r >= 0; r--) {
+        real xr = k->X[r];
+        if (r != rlast) {
+            if (!propagate(&st, x, xr, k->kB, k->smax)) break;
+            x = xr;
+        }
+        if (FABS(st.p[0]) > xr * k->th + k->margin) break;
+        residual_cov_inv(&st, k, &g);
+        int32_t b = search_row(S, k, Y, Zc, &st, r, &g, &chi2, buf);
+        if (b >= 0 && chi2 <= k->chi2max) {
+            chi2sum = chi2sum + chi2;
+            kf_update(&st, &g, Y[b], Zc[b]);
+            S->cnt[ORC_INFO_UPDATES]++;
+            hits[n++] = b;
+            inner = st;
+            xin = x;
+            miss = 0;
+        } else if (++miss >= k->max_miss) {
+            break;
+        }
+    }
+    int ndf = 2 * n - 5;
+    res->tl_nhits[t] = n;
+    res->tl_ndf[t] = ndf;
+    for (int i = 0; i < 5; i++) res->tl_par[t * 5 + i] = (double)inner.p[i];
+    int q = 0;
+    for (int i = 0; i < 5; i++)
+        for (int j = 0; j <= i; j++) res->tl_cov[t * 15 + q++] = (double)inner.C[i][j];
+    res->tl_x[t] = (double)xin;
+    res->tl_chi2[t] = (double)chi2sum;
+    if (ndf >= 1) {
+        /* Section 3.1: w = n * (alpha - chi2/beta), chi2 read as chi2 per degree of freedom */
+        real w = (real)n * (k->alpha - (chi2sum / (real)ndf) / k->beta);
+        res->tl_w[t] = (double)w;
+    }
+}
+
+/* A6 selection and A7 output order for one sector. */
+static void sector_select(Sector *S, const K *k, orc_result *res, int64_t t0, const real *wv)
+{
+    int nr = k->nr;
+    int64_t T = S->nstarts;
+    /* each cluster goes to the tracklet of maximal weight; equal weights: the earlier tracklet */
+    for (int64_t i = 0; i < T; i++) {
+        int64_t t = t0 + i;
+        if (res->tl_ndf[t] < 1) continue;
+        const int32_t *h = res->tl_hits + (size_t)t * (size_t)nr;
+        for (int j = 0; j < res->tl_nhits[t]; j++) {
+            int32_t c = h[j];
+            int32_t o = res->owner[c];
+            if (o < 0 || wv[t] > wv[o]) res->owner[c] = (int32_t)t;
+        }
+    }
+    int64_t *keys = (int64_t *)malloc(sizeof(int64_t) * 2 * (size_t)(T > 0 ? T : 1));
+    int64_t na = 0;
+    for (int64_t i = 0; i < T; i++) {
+        int64_t t = t0 + i;
+        if (res->tl_ndf[t] < 1) continue;
+        const int32_t *h = res->tl_hits + (size_t)t * (size_t)nr;
+        int own = 0;
+        int32_t inner = -1;
+        for (int j = 0; j < res->tl_nhits[t]; j++)
+            if (res->owner[h[j]] == (int32_t)t) {
+                own++;
+                inner = h[j];               /* hits are stored outer to inner */
+            }
+        res->tl_nowned[t] = own;
+        real q = (real)res->tl_par[t * 5 + 4];
+        int acc = own >= k->min_clusters && FABS(q) <= k->qptmax;
+        res->tl_accept[t] = (uint8_t)acc;
+        if (acc) {
+            keys[2 * na] = inner;           /* Section 3.2: sort by the innermost cluster */
+            keys[2 * na + 1] = t;
+            na++;
+        }
+    }
+    qsort(keys, (size_t)na, 2 * sizeof(int64_t), cmp_i64pair);
+    S->ntracks = na;
+    S->tracks = (int32_t *)malloc(sizeof(int32_t) * (size_t)(na > 0 ? na : 1));
+    for (int64_t i = 0; i < na; i++) S->tracks[i] = (int32_t)keys[2 * i + 1];
+    free(keys);
+}
+
+orc_result *SFX(orc_track_event)(const orc_config *cfg, const double *y, const double *z,
+                                 const uint8_t *row, const int32_t *counts, int64_t n)
+{
+    K k;
+    make_consts(&k, cfg);
+    int nr = k.nr, ns = cfg->n_sectors;
+    orc_result *res = orc_result_alloc(n, nr);
+    real *Y = (real *)malloc(sizeof(real) * (size_t)(n > 0 ? n : 1));
+    real *Zc = (real *)malloc(sizeof(real) * (size_t)(n > 0 ? n : 1));
+    for (int64_t i = 0; i < n; i++) {
+        Y[i] = (real)y[i];
+        Zc[i] = (real)z[i];
+    }
+    Sector *S = (Sector *)calloc((size_t)ns, sizeof(Sector));
+    int64_t off = 0;
+    int maxrow = 1;
+    for (int s = 0; s < ns; s++) {
+        S[s].rows = (Row *)calloc((size_t)nr, sizeof(Row));
+        S[s].off = off;
+        for (int r = 0; r < nr; r++) {
+            int32_t cnt = counts[s * nr + r];
+            S[s].rows[r].off = off;
+            S[s].rows[r].n = cnt;
+            off += cnt;
+            if (cnt > maxrow) maxrow = cnt;
+        }
+        S[s].n = off - S[s].off;
+    }
+#ifdef _OPENMP
+    int nth = cfg->n_threads > 0 ? cfg->n_threads : omp_get_max_threads();
+#endif
+
+#ifdef _OPENMP
+#pragma omp parallel num_threads(nth)
+#endif
+    {
+        int32_t *bu = (int32_t *)malloc(sizeof(int32_t) * (size_t)maxrow);
+        int32_t *bd = (int32_t *)malloc(sizeof(int32_t) * (size_t)maxrow);
+#ifdef _OPENMP
+#pragma omp for schedule(dynamic, 1)
+#endif
+        for (int s = 0; s < ns; s++) sector_links(&S[s], &k, Y, Zc, row, res, bu, bd);
+        free(bu);
+        free(bd);
+    }
+
+    int64_t T = 0;
+    for (int s = 0; s < ns; s++) T += S[s].nstarts;
+    orc_result_alloc_tracklets(res, T);
+    int64_t *t0 = (int64_t *)malloc(sizeof(int64_t) * (size_t)(ns + 1));
+    t0[0] = 0;
+    for (int s = 0; s < ns; s++) {
+        t0[s + 1] = t0[s] + S[s].nstarts;
+        for (int64_t i = 0; i < S[s].nstarts; i++) res->starts[t0[s] + i] = S[s].starts[i];
+    }
+    real *wv = (real *)malloc(sizeof(real) * (size_t)(T > 0 ? T : 1));
+
+#ifdef _OPENMP
+#pragma omp parallel num_threads(nth)
+#endif
+    {
+        int32_t *buf = (int32_t *)malloc(sizeof(int32_t) * (size_t)maxrow);
+        int32_t *chain = (int32_t *)malloc(sizeof(int32_t) * (size_t)nr);
+#ifdef _OPENMP
+#pragma omp for schedule(dynamic, 1)
+#endif
+        for (int s = 0; s < ns; s++) {
+            for (int64_t i = 0; i < S[s].nstarts; i++) {
+                int64_t t = t0[s] + i;
+                construct(&S[s], &k, Y, Zc, row, res, t, S[s].starts[i], buf, chain);
+                wv[t] = (real)res->tl_w[t];
+            }
+            sector_select(&S[s], &k, res, t0[s], wv);
+        }
+        free(buf);
+        free(chain);
+    }
+
+    /* A7: concatenate sectors (input indices are grouped by sector, so this is the
+     * canonical order), hits from the innermost to the outermost row */
+    int64_t M = 0, H = 0;
+    for (int s = 0; s < ns; s++) {
+        M += S[s].ntracks;
+        for (int64_t i = 0; i < S[s].ntracks; i++) H += res->tl_nowned[S[s].tracks[i]];
+    }
+    res->n_tracks = M;
+    res->n_track_hits = H;
+    res->trk_hits = (int32_t *)malloc(sizeof(int32_t) * (size_t)(H > 0 ? H : 1));
+    int64_t m = 0, h = 0;
+    for (int s = 0; s < ns; s++) {
+        for (int64_t i = 0; i < S[s].ntracks; i++) {
+            int32_t t = S[s].tracks[i];
+            res->trk_tracklet[m] = t;
+            res->trk_first[m] = (int32_t)h;
+            res->trk_nhits[m] = res->tl_nowned[t];
+            const int32_t *hh = res->tl_hits + (size_t)t * (size_t)nr;
+            for (int j = res->tl_nhits[t] - 1; j >= 0; j--)
+                if (res->owner[hh[j]] == t) res->trk_hits[h++] = hh[j];
+            m++;
+        }
+    }
+    for (int s = 0; s < ns; s++)
+        for (int i = 0; i < ORC_INFO_COUNT; i++) res->counters[i] += S[s].cnt[i];
+
+    for (int s = 0; s < ns; s++) {
+        for (int r = 0; r < nr; r++) {
+            free(S[s].rows[r].cstart);
+            free(S[s].rows[r].sorted);
+        }
+        free(S[s].rows);
+        free(S[s].starts);
+        free(S[s].tracks);
+    }
+    free(S);
+    free(t0);
+    free(wv);
+    free(Y);
+    free(Zc);
+    free(k.X);
+    return res;
+}
+
+/* ----------------------------------------------------------------------------------------- */
+/* pieces exposed for pins                                                                    */
+/* ----------------------------------------------------------------------------------------- */
+int SFX(orc_propagate)(double *state, double *cov15, double x0, double x1, double bz, double sin_max)
+{
+    KS s;
+    for (int i = 0; i < 5; i++) s.p[i] = (real)state[i];
+    int q = 0;
+    for (int i = 0; i < 5; i++)
+        for (int j = 0; j <= i; j++) {
+            s.C[i][j] = s.C[j][i] = (real)cov15[q];
+            q++;
+        }
+    int ok = propagate(&s, (real)x0, (real)x1, (real)(-ORC_KAPPA * bz), (real)sin_max);
+    for (int i = 0; i < 5; i++) state[i] = (double)s.p[i];
+    q = 0;
+    for (int i = 0; i < 5; i++)
+        for (int j = 0; j <= i; j++) cov15[q++] = (double)s.C[i][j];
+    return ok;
+}
+
+#ifndef ORC_F32
+int orc_seed_f64(const double *x3, const double *y3, const double *z3, double bz, double sin_max,
+                 double *state)
+{
+    return seed3(x3, y3, z3, -ORC_KAPPA * bz, sin_max, state);
+}
+#endif
+
+#ifdef ORC_F32
+void orc_bin_row_f32(const double *y, const double *z, int n, float ymin, float zmin, float inv_dy,
+                     float inv_dz, int ny, int nz, int32_t *cell, int32_t *perm, int32_t *cell_start)
+{
+    int nc = ny * nz;
+    for (int c = 0; c <= nc; c++) cell_start[c] = 0;
+    for (int i = 0; i < n; i++) {
+        int iy = cell1((float)y[i], ymin, inv_dy, ny);
+        int iz = cell1((float)z[i], zmin, inv_dz, nz);
+        cell[i] = iz * ny + iy;
+        cell_start[cell[i] + 1]++;
+    }
+    for (int c = 0; c < nc; c++) cell_start[c + 1] += cell_start[c];
+    int32_t *fill = (int32_t *)malloc(sizeof(int32_t) * (size_t)(nc > 0 ? nc : 1));
+    for (int c = 0; c < nc; c++) fill[c] = cell_start[c];
+    for (int i = 0; i < n; i++) perm[fill[cell[i]]++] = i;
+    free(fill);
+}
+#endif
