@@ -470,28 +470,26 @@ static void construct(Sector *S, const K *k, const real *Y, const real *Zc, cons
     Gain g;
     real chi2;
 
-    /* outward pass */
+    /* Outward pass.  `st` is the state at the last fitted cluster (at x = xs); the
+     * prediction for row r is that state transported along the helix to x_r. */
     int r0 = rowv[c0];
-    real x = k->X[r0];
-    KS last = st;
-    real xlast = x;
+    real xs = k->X[r0];
     int rlast = -1, miss = 0, nup = 0;
+    KS pr;
     for (int r = r0; r < nr; r++) {
         real xr = k->X[r];
-        if (r != r0) {
-            if (!propagate(&st, x, xr, k->kB, k->smax)) break;
-            x = xr;
-        }
-        if (FABS(st.p[0]) > xr * k->th + k->margin) break;
-        residual_cov_inv(&st, k, &g);
-        int32_t b = search_row(S, k, Y, Zc, &st, r, &g, &chi2, buf);
+        pr = st;
+        if (xr != xs && !propagate(&pr, xs, xr, k->kB, k->smax)) break;
+        if (FABS(pr.p[0]) > xr * k->th + k->margin) break;
+        residual_cov_inv(&pr, k, &g);
+        int32_t b = search_row(S, k, Y, Zc, &pr, r, &g, &chi2, buf);
         if (b >= 0 && chi2 <= k->chi2max) {
-            kf_update(&st, &g, Y[b], Zc[b]);
+            kf_update(&pr, &g, Y[b], Zc[b]);
             S->cnt[ORC_INFO_UPDATES]++;
+            st = pr;
+            xs = xr;
             nup++;
             rlast = r;
-            last = st;
-            xlast = x;
             miss = 0;
         } else if (++miss >= k->max_miss) {
             break;
@@ -500,36 +498,33 @@ static void construct(Sector *S, const K *k, const real *Y, const real *Zc, cons
     res->tl_nup[t] = nup;
     if (rlast < 0) return;
 
-    /* inward pass from the outermost cluster, covariance reset to the seed's */
-    st = last;
+    /* Inward pass from the outermost cluster, covariance reset to the seed's; its
+     * clusters are the tracklet's, its last state is reported. */
     set_diag(&st, k->cov0);
-    x = xlast;
     miss = 0;
     int n = 0;
     real chi2sum = 0;
-    KS inner = st;
-    real xin = x;
     for (int r = rlast; r >= 0; r--) {
         real xr = k->X[r];
-        if (r != rlast) {
-            if (!propagate(&st, x, xr, k->kB, k->smax)) break;
-            x = xr;
-        }
-        if (FABS(st.p[0]) > xr * k->th + k->margin) break;
-        residual_cov_inv(&st, k, &g);
-        int32_t b = search_row(S, k, Y, Zc, &st, r, &g, &chi2, buf);
+        pr = st;
+        if (xr != xs && !propagate(&pr, xs, xr, k->kB, k->smax)) break;
+        if (FABS(pr.p[0]) > xr * k->th + k->margin) break;
+        residual_cov_inv(&pr, k, &g);
+        int32_t b = search_row(S, k, Y, Zc, &pr, r, &g, &chi2, buf);
         if (b >= 0 && chi2 <= k->chi2max) {
             chi2sum = chi2sum + chi2;
-            kf_update(&st, &g, Y[b], Zc[b]);
+            kf_update(&pr, &g, Y[b], Zc[b]);
             S->cnt[ORC_INFO_UPDATES]++;
+            st = pr;
+            xs = xr;
             hits[n++] = b;
-            inner = st;
-            xin = x;
             miss = 0;
         } else if (++miss >= k->max_miss) {
             break;
         }
     }
+    KS inner = st;
+    real xin = xs;
     int ndf = 2 * n - 5;
     res->tl_nhits[t] = n;
     res->tl_ndf[t] = ndf;
