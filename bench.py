@@ -1,0 +1,338 @@
+#!/usr/bin/env python
+"""Throughput of the CUDA TPC sector tracker on the central-like workload.
+
+One step = one central-like event (16000 primaries + 3000 secondaries, 20 % noise, 36
+sectors x 159 rows, about 3.3 M clusters) through every stage of the hot path: ingest and
+per-row grids, neighbours finder, evolution and start hits, tracklet construction,
+selection, output in canonical order.  Inputs are resident in HBM before the timed region;
+L2 is flushed (512 MB write, not timed) before every step; each step is timed with CUDA
+events on the tracker's stream and the step times are summed.
+
+Prints one JSON line (rank 0).  ``--impl reference`` times the CPU oracle (the reference
+arm of this build) on the host cores instead.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "central-like events/s"
+WORKLOAD = ("central-like event: 16000 primary + 3000 secondary helices (vertex radius U[0,60] cm), "
+            "pT > 0.05 GeV, 20% noise, 36 sectors x 159 pad rows, Bz 0.5 T, seed 1")
+PROFILE_JSON = os.path.join(ROOT, "profiles", "construct_traffic.json")
+CONSTRUCT_SRC = os.path.join(ROOT, "paper_1712_09407_gb300", "csrc", "k_construct.cu")
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    return ap.parse_args()
+
+
+def dist_env():
+    return int(os.environ.get("RANK", 0)), int(os.environ.get("WORLD_SIZE", 1)), int(os.environ.get("LOCAL_RANK", 0))
+
+
+# ------------------------------------------------------------------------------------------------
+# clocks during the timed region
+# ------------------------------------------------------------------------------------------------
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+              "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+              "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.FIELDS,
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except OSError:
+            self.proc = None
+        time.sleep(0.3)
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        rows = []
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) >= 9:
+                rows.append(parts)
+        os.unlink(self.path)
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+
+        def num(x):
+            try:
+                return float(x)
+            except ValueError:
+                return None
+        sm = [num(r[1]) for r in rows if num(r[1])]
+        mx = max(num(r[2]) or 0 for r in rows)
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if r[5 + i].lower().startswith("active")})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": mx, "reasons": reasons,
+                "samples": len(rows), "power_w_max": max(num(r[3]) or 0 for r in rows)}
+
+
+# ------------------------------------------------------------------------------------------------
+# roofline bookkeeping
+# ------------------------------------------------------------------------------------------------
+def measured_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        d = json.load(open(p))
+        return float(d["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+def construct_bytes(stats):
+    """Algorithmic bytes of one tracklet-construction launch (A5):
+    per row visit 16 B unit metadata + 8 B grid size + 16 B grid origin/scale + 8 B per
+    z-row of cells (2 cell starts) + 8 B per cluster read from the cells; per tracklet a
+    16 B start record, three 8 B seed points, 4 B input index, 100 B of results and 4 B per
+    fitted cluster (taken as 2 per visit of the inward pass, bounded by the visit count)."""
+    V, K, T = stats["row_visits"], stats["candidates"], stats["tracklets"]
+    return V * (16 + 8 + 16 + 8) + 8 * K + T * (16 + 24 + 4 + 100) + 4 * V // 2
+
+
+def traffic_for_current_kernel():
+    if not os.path.exists(PROFILE_JSON):
+        return None, None
+    d = json.load(open(PROFILE_JSON))
+    h = hashlib.sha256(open(CONSTRUCT_SRC, "rb").read()).hexdigest()[:16]
+    if d.get("source_sha256_16") != h:
+        return None, "kernel changed since capture"
+    return d.get("dram_bytes_per_launch"), d.get("note")
+
+
+# ------------------------------------------------------------------------------------------------
+# CPU oracle legs
+# ------------------------------------------------------------------------------------------------
+def oracle_timing(ev, min_seconds=10.0, max_runs=5, min_runs=1):
+    import oracle
+    cfg = oracle.config_for(ev.geometry)
+    times = []
+    t_total = time.perf_counter()
+    while len(times) < max_runs and (len(times) < min_runs or time.perf_counter() - t_total < min_seconds):
+        t0 = time.perf_counter()
+        oracle.track_event(cfg, ev.y, ev.z, ev.row, ev.counts, precision=32)
+        times.append(time.perf_counter() - t0)
+    cores = os.cpu_count()
+    return dict(value=len(times) / sum(times), unit="events/s", cores=cores, kind="oracle",
+                sample="full central-like event (3.29 M clusters), float-mode C oracle, OpenMP over the 36 "
+                       "sectors on %d threads, %d runs, %.1f s" % (cores, len(times), sum(times)))
+
+
+def run_reference(args):
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return 0
+    from paper_1712_09407_gb300 import eventgen
+    import oracle
+    oracle.build()
+    ev = eventgen.config_event(2)
+    cfg = oracle.config_for(ev.geometry)
+    for _ in range(args.warmup):
+        oracle.track_event(cfg, ev.y, ev.z, ev.row, ev.counts, precision=32)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        oracle.track_event(cfg, ev.y, ev.z, ev.row, ev.counts, precision=32)
+    dt = time.perf_counter() - t0
+    v = args.steps / dt
+    cores = os.cpu_count()
+    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": "events/s", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt * 1e3 / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+            "data": "synthetic", "config": {"workload": WORKLOAD, "clusters_per_event": ev.n},
+            "cpu_baseline": {"value": v, "unit": "events/s", "cores": cores, "kind": "oracle",
+                             "sample": "full central-like event per step, float-mode C oracle, OpenMP over "
+                                       "36 sectors on %d host threads" % cores},
+            "e2e": {"value": v, "unit": "events/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+    return 0
+
+
+# ------------------------------------------------------------------------------------------------
+# our arm
+# ------------------------------------------------------------------------------------------------
+def run_ours(args):
+    import torch
+
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    from __graft_entry__ import build
+    build()
+    from paper_1712_09407_gb300 import eventgen
+    from paper_1712_09407_gb300.tracker import Tracker
+
+    ev = eventgen.config_event(2, event=rank)           # one replica per GPU, its own event
+    tr = Tracker.for_geometry(ev.geometry)
+    tr.reserve(ev.n, 1)
+    stream = torch.cuda.Stream()
+    y = torch.from_numpy(ev.y).cuda()
+    z = torch.from_numpy(ev.z).cuda()
+    row = torch.from_numpy(ev.row).cuda()
+    flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+    torch.cuda.synchronize()
+
+    with torch.cuda.stream(stream):
+        for _ in range(args.warmup):
+            r = tr.track(y, z, row, ev.counts, stream=stream)
+            r.sync()
+            r.release()
+
+    def barrier():
+        torch.cuda.synchronize()
+        if world > 1:
+            torch.distributed.barrier()
+        torch.cuda.synchronize()
+
+    tr.set_timing(True)
+    clocks = ClockSampler(local)
+    clocks.start()
+    barrier()
+    t_wall = time.perf_counter()
+    starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    stage_ms = np.zeros(7)
+    launches = 0
+    stats = None
+    results = []
+    with torch.cuda.stream(stream):
+        for k in range(args.steps):
+            flush.fill_(float(k))                      # evict L2 (not timed)
+            starts[k].record(stream)
+            results.append(tr.track(y, z, row, ev.counts, stream=stream))
+            ends[k].record(stream)
+    barrier()
+    wall = time.perf_counter() - t_wall
+    clk = clocks.stop()
+    for r in results:
+        r.sync()
+        stats = r.stats()
+        stage_ms += np.array(stats["ms"])
+        launches += stats["kernel_launches"]
+        r.release()
+    del results
+    step_ms = [s.elapsed_time(e) for s, e in zip(starts, ends)]
+    total_s = sum(step_ms) / 1e3
+    if world > 1:
+        t = torch.tensor([total_s], device="cuda")
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        total_s = float(t.item())
+    value = world * args.steps / total_s
+    tr.set_timing(False)
+
+    # ---- end to end through the host-buffer entry point
+    e2e = None
+    if not args.no_e2e:
+        hy = torch.from_numpy(ev.y).pin_memory()
+        hz = torch.from_numpy(ev.z).pin_memory()
+        hr = torch.from_numpy(ev.row).pin_memory()
+        bufs = None
+        times = []
+        h2d = d2h = 0
+        with torch.cuda.stream(stream):
+            for k in range(args.warmup + args.steps):
+                flush.fill_(float(k))
+                torch.cuda.synchronize()
+                t0 = time.perf_counter()
+                r = tr.track_host(hy, hz, hr, ev.counts, stream=stream)
+                M, H = r.sync()
+                if bufs is None or bufs["par"].shape[0] < M or bufs["hits"].shape[0] < H:
+                    bufs = dict(par=torch.empty((M + 1024, 5)).pin_memory(), cov=torch.empty((M + 1024, 15)).pin_memory(),
+                                x_ref=torch.empty(M + 1024).pin_memory(), alpha=torch.empty(M + 1024).pin_memory(),
+                                chi2=torch.empty(M + 1024).pin_memory(),
+                                **{n: torch.empty(M + 1024, dtype=torch.int32).pin_memory()
+                                   for n in ("ndf", "nhits", "first", "sector", "event")},
+                                hits=torch.empty(H + 65536, dtype=torch.int32).pin_memory())
+                from paper_1712_09407_gb300.tracker import tpc_result_copy_to_host
+                tpc_result_copy_to_host(r.handle, bufs)
+                t1 = time.perf_counter()
+                r.release()
+                if k >= args.warmup:
+                    times.append(t1 - t0)
+                h2d = ev.n * 9
+                d2h = M * (5 + 15 + 3 + 5) * 4 + H * 4 + 48
+        e2e_v = len(times) / sum(times)
+        if world > 1:
+            t = torch.tensor([sum(times)], device="cuda")
+            torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+            e2e_v = world * len(times) / float(t.item())
+        e2e = {"value": e2e_v, "unit": "events/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
+               "path": "tpc_track_event_host (pinned host input) + tpc_result_copy_to_host, wall clock"}
+
+    if rank != 0:
+        return 0
+    names = ["setup", "ingest", "neighbours", "evolution", "construction", "selection", "output"]
+    mean_stage = stage_ms / args.steps
+    stages = {n: round(float(v), 4) for n, v in zip(names, mean_stage)}
+    peak, peak_kind = measured_peaks()
+    cb = construct_bytes(stats)
+    con_ms = mean_stage[4]
+    achieved = cb / (con_ms * 1e-3) / 1e9
+    traffic, tnote = traffic_for_current_kernel()
+    roof = {"kernel": "k_construct (A5 tracklet construction)", "bound": "hbm", "achieved": achieved,
+            "peak": peak, "unit": "GB/s", "frac": achieved / peak, "peak_source": peak_kind + " (hbm_gbs)",
+            "traffic": traffic, "algorithmic_bytes": cb, "launch_ms": con_ms,
+            "units": {"row_visits": stats["row_visits"], "tracklets": stats["tracklets"],
+                      "candidates": stats["candidates"]}}
+    if tnote:
+        roof["traffic_note"] = tnote
+    line = {"metric": METRIC, "value": value, "unit": "events/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": 1e3 * total_s / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "clusters_per_event": ev.n,
+                       "l2": "flushed before every step (512 MB write, untimed)",
+                       "parallelism": "replicas" if world > 1 else "single GPU"},
+            "clusters_per_s": value * ev.n, "tracks_per_event": stats["tracks"], "stages_ms": stages,
+            "gpu_launches": launches, "e2e": e2e, "roofline": roof, "clocks": clk,
+            "wall_s_timed_region": wall}
+    if world == 1 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = oracle_timing(ev)
+    print(json.dumps(line))
+    return 0
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,272 @@
+/* tpcca.h — C ABI of the GB300 TPC sector tracker.
+ *
+ * Implements the sector tracker of Rohr et al., "ALICE HLT TPC Tracking of
+ * Pb-Pb Events on GPUs": clusters measured on the 159 pad rows of each of the
+ * 36 TPC sectors go in (Section 1: "reconstructed clusters are sent to the
+ * sector tracker which reconstructs the tracks in each TPC sector
+ * individually"); per-track parameters, covariances and the list of the
+ * clusters of each track come out (Section 3.3: the sector tracker "outputs a
+ * list of clusters for each track").  Between them run the steps of Section 1
+ * (neighbours finder, evolution, tracklets from chains of one-to-one links,
+ * Kalman tracklet construction, tracklet selection) with the cluster weight of
+ * Section 3.1, the track sorting of Section 3.2 and the 30-cluster minimum of
+ * Section 5, all as CUDA kernels for sm_103a.
+ *
+ * Conventions
+ *  - Every function returns an int status (TPC_OK = 0) unless stated otherwise;
+ *    nothing throws across this boundary.
+ *  - "device" pointers are CUDA global-memory pointers of the current device;
+ *    "host" pointers are ordinary (or pinned) host memory.
+ *  - Streams are passed as `void *` holding a cudaStream_t (NULL = legacy
+ *    default stream).  All device work of a call is ordered on that stream.
+ *  - Cluster input layout (SoA): y[i], z[i] float32 (cm, sector-local frame:
+ *    x along the sector centre, y in r-phi, z global), row[i] uint8 pad row.
+ *    Clusters are grouped by sector, then by row: counts[s * n_rows + r] is the
+ *    number of clusters of sector s on row r, and they follow each other in
+ *    that order.  Order inside one (sector, row) group is free.
+ *  - Track parameters are (y, z, sin phi, tan lambda, q/pT) at the plane x of
+ *    the track's innermost cluster, in its sector's frame; curvature is
+ *    -kappa * Bz * q/pT with kappa = 2.99792458e-3 GeV/(T cm).  Covariances are
+ *    15 floats: the lower triangle, row-major, of the 5x5 matrix in that order.
+ */
+#ifndef TPCCA_H
+#define TPCCA_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* Status codes. */
+enum {
+    TPC_OK = 0,
+    TPC_ERR_INVALID_ARG = 1,   /* bad pointer, counts not summing to n, a cluster on the wrong row */
+    TPC_ERR_CAPACITY = 2,      /* a device pool overflowed; tpc_last_error_detail says where */
+    TPC_ERR_BUDGET = 3,        /* the call would exceed the tracker's HBM budget */
+    TPC_ERR_TIMEOUT = 4,       /* a bounded device-side wait expired */
+    TPC_ERR_CUDA = 5,          /* a CUDA runtime call failed */
+    TPC_ERR_STATE = 6          /* wrong call order (e.g. reading a result before it was produced) */
+};
+
+/* Pipeline stages, as reported by tpc_last_error_detail. */
+enum {
+    TPC_STAGE_NONE = 0,
+    TPC_STAGE_INGEST = 1,      /* A1 cluster ingest and per-row grids */
+    TPC_STAGE_NEIGHBOURS = 2,  /* A2 */
+    TPC_STAGE_EVOLUTION = 3,   /* A3 + A4 */
+    TPC_STAGE_CONSTRUCTION = 4,/* A5 */
+    TPC_STAGE_SELECTION = 5,   /* A6 */
+    TPC_STAGE_OUTPUT = 6       /* A7 */
+};
+
+/* Detector geometry (Section 1: two volumes of 18 trapezoidal sectors, 159 pad rows).
+ * row_x: host array of n_rows row positions (cm), strictly increasing, copied at create.
+ * n_sectors: 36 (z >= 0 for sectors 0-17, z < 0 for 18-35) or 1 (one phi sector
+ * spanning both z halves). */
+typedef struct {
+    int n_rows;
+    const float *row_x;
+    float tan_half;            /* tan of the sector half-opening, tan(10 deg) */
+    float z_max;               /* half-length of the drift volume (cm) */
+    int n_sectors;
+} tpc_geometry;
+
+/* Tracker constants.  alpha = 6 (Section 3.1) and min_clusters = 30 (Section 5)
+ * are the paper's; every other default is a reading of a point the paper leaves
+ * open (see tpc_params_default). */
+typedef struct {
+    float sigma_y, sigma_z;    /* cluster errors (cm) */
+    float nb_ty, nb_tz;        /* neighbours finder window: |dy| <= ty*dx, |dz| <= tz*dx */
+    float nb_gate;             /* straight-line gate: score <= nb_gate * (1 + wd^2 + wu^2) */
+    int min_chain;             /* clusters in a chain of one-to-one links to start a tracklet */
+    float seed_cov[5];         /* diagonal of the seed covariance */
+    float win_nsigma;          /* construction search window half-width in sigmas */
+    float chi2_max;            /* 2-dof chi2 gate for a cluster */
+    int max_miss;              /* consecutive rows without a cluster that end a pass */
+    float edge_margin;         /* a pass ends when |y| > x * tan_half + edge_margin */
+    float sin_max;             /* a pass ends when |sin phi| reaches sin_max */
+    float alpha, beta;         /* cluster weight w = n * (alpha - (chi2/ndf) / beta) */
+    int min_clusters;          /* minimum clusters of a track */
+    float qpt_max;             /* low-momentum cut: |q/pT| <= qpt_max */
+} tpc_params;
+
+/* Launch and grid choices.  None of them changes any result (every search
+ * enumerates all grid cells that overlap its window and applies the exact window
+ * test), so the autotuner may pick them freely. */
+typedef struct {
+    float bin_occupancy;       /* target clusters per grid cell (>0) */
+    int neighbours_block;      /* threads per CTA of the neighbours finder (multiple of 32, <= 256) */
+    int construct_block;       /* threads per CTA of the tracklet constructor (multiple of 32, <= 256) */
+    int construct_ctas_per_sm; /* persistent CTAs per SM of the constructor (0 = occupancy limit) */
+    int stage_rows;            /* 1: stage rows k-1, k+1 into shared memory with bulk copies */
+} tpc_tuning;
+
+typedef struct tpc_tracker tpc_tracker;
+typedef struct tpc_result tpc_result;
+
+/* Read-only view of a finished result.  All pointers are device pointers owned by
+ * the result; they stay valid until tpc_result_release.  Track m's clusters are
+ * hits[first[m] .. first[m] + nhits[m]), ordered from the innermost to the
+ * outermost row, given as indices into the call's input arrays (for a batch: into
+ * the concatenated input).  Tracks are sorted by (event, sector, row and input
+ * index of their innermost cluster) (Section 3.2). */
+typedef struct {
+    int64_t n_tracks;
+    int64_t n_hits;
+    const float *par;          /* [n_tracks * 5] */
+    const float *cov;          /* [n_tracks * 15] */
+    const float *x_ref;        /* [n_tracks] x of the innermost cluster */
+    const float *alpha;        /* [n_tracks] sector centre azimuth (rad) */
+    const float *chi2;         /* [n_tracks] sum of the Kalman update chi2 */
+    const int32_t *ndf;        /* [n_tracks] 2 * fitted clusters - 5 */
+    const int32_t *nhits;      /* [n_tracks] clusters kept by the track */
+    const int32_t *first;      /* [n_tracks] offset into hits */
+    const int32_t *sector;     /* [n_tracks] sector within its event */
+    const int32_t *event;      /* [n_tracks] event within the batch */
+    const int32_t *hits;       /* [n_hits] input cluster indices */
+} tpc_track_view;
+
+/* Fill *p with the default constants.  Never fails. */
+void tpc_params_default(tpc_params *p);
+
+/* Fill *t with the default launch choices.  Never fails. */
+void tpc_tuning_default(tpc_tuning *t);
+
+/* Create a tracker on the current CUDA device.
+ * geometry: host struct, copied.  bz_tesla: solenoid field.
+ * params: host struct or NULL for tpc_params_default.
+ * hbm_budget: bytes of device memory the tracker may hold (workspace plus live
+ *   results); 0 = no limit.  Work that would exceed it fails with TPC_ERR_BUDGET.
+ * *out receives the handle (owned by the caller; free with tpc_tracker_destroy).
+ * Errors: TPC_ERR_INVALID_ARG (NULL out/geometry, n_rows outside 3..255, row_x not
+ * increasing, n_sectors not 1 or 36), TPC_ERR_CUDA. */
+int tpc_tracker_create(const tpc_geometry *geometry, float bz_tesla, const tpc_params *params,
+                       size_t hbm_budget, tpc_tracker **out);
+
+/* Replace the launch choices (host struct, copied).  Results are unchanged. */
+int tpc_tracker_set_tuning(tpc_tracker *tr, const tpc_tuning *t);
+
+/* Pre-size the device workspace for batches of up to max_clusters clusters and
+ * max_events events, so that later calls of that size allocate nothing.
+ * Errors: TPC_ERR_BUDGET, TPC_ERR_CUDA. */
+int tpc_tracker_reserve(tpc_tracker *tr, int64_t max_clusters, int max_events);
+
+/* Track one event (Section 1; all 36 sectors).  y, z, row: device arrays of n
+ * clusters, owned by the caller, which must keep them valid until the stream has
+ * passed this call's work.  counts: HOST array of n_sectors * n_rows counts in
+ * the grouped order described above; it is read before the call returns.
+ * The work is enqueued on `stream`; *out receives a result handle whose data is
+ * valid once tpc_result_sync_counts has returned TPC_OK.
+ * Calls on one tracker are ordered: a call waits (on the device) for the previous
+ * call's use of the shared workspace.
+ * Errors: TPC_ERR_INVALID_ARG (counts not summing to n, n < 0, NULL pointers with
+ * n > 0), TPC_ERR_BUDGET, TPC_ERR_CUDA.  Device-side errors (a cluster on the
+ * wrong row, pool overflow, timeout) are reported by tpc_result_sync_counts. */
+int tpc_track_event(tpc_tracker *tr, const float *y, const float *z, const uint8_t *row,
+                    const int32_t *counts, int64_t n, void *stream, tpc_result **out);
+
+/* Track n_events events in one pass of every stage (each stage is one launch over
+ * all sectors of all events).  The events' clusters are concatenated in y, z,
+ * row (device, n_total clusters); counts (host) holds n_events * n_sectors *
+ * n_rows counts, event-major.  Results are identical to one call per event.
+ * Errors as tpc_track_event. */
+int tpc_track_batch(tpc_tracker *tr, const float *y, const float *z, const uint8_t *row,
+                    const int32_t *counts, int n_events, int64_t n_total, void *stream,
+                    tpc_result **out);
+
+/* Same as tpc_track_event, but y, z, row are HOST arrays: the call copies them to
+ * the device on `stream` (from pinned memory when the caller's buffers are
+ * pinned) before tracking. */
+int tpc_track_event_host(tpc_tracker *tr, const float *y, const float *z, const uint8_t *row,
+                         const int32_t *counts, int64_t n, void *stream, tpc_result **out);
+
+/* Wait for the result's work and return its track and hit counts (either pointer
+ * may be NULL).  Returns the device-side status of the call: TPC_OK,
+ * TPC_ERR_INVALID_ARG (a cluster's row byte disagrees with counts),
+ * TPC_ERR_CAPACITY, TPC_ERR_TIMEOUT, or TPC_ERR_CUDA. */
+int tpc_result_sync_counts(tpc_result *res, int64_t *n_tracks, int64_t *n_hits);
+
+/* Fill *view with device pointers to the result.  Requires a successful
+ * tpc_result_sync_counts first (TPC_ERR_STATE otherwise). */
+int tpc_result_get(tpc_result *res, tpc_track_view *view);
+
+/* Copy the whole result to host buffers sized from tpc_result_sync_counts
+ * (any pointer may be NULL to skip that array).  Synchronous. */
+int tpc_result_copy_to_host(tpc_result *res, float *par, float *cov, float *x_ref, float *alpha,
+                            float *chi2, int32_t *ndf, int32_t *nhits, int32_t *first,
+                            int32_t *sector, int32_t *event, int32_t *hits);
+
+/* Release a result and its device memory (stream-ordered on the call's stream).
+ * NULL is ignored. */
+void tpc_result_release(tpc_result *res);
+
+/* Destroy a tracker after its outstanding work finishes.  NULL is ignored.
+ * Results created by the tracker must be released first. */
+void tpc_tracker_destroy(tpc_tracker *tr);
+
+/* Static text for a status code; never NULL. */
+const char *tpc_status_string(int status);
+
+/* Where the last device-side error of the tracker happened (each pointer may be
+ * NULL): event index in the batch, sector, and TPC_STAGE_* of the stage.
+ * Returns that error's status (TPC_OK if none). */
+int tpc_last_error_detail(tpc_tracker *tr, int *event, int *sector, int *stage);
+
+/* Statistics of one call.  ms[] holds device milliseconds per stage, measured with
+ * CUDA events on the call's stream when timing was enabled for the call (zeros
+ * otherwise): ms[0] set-up copies and clears, ms[TPC_STAGE_INGEST .. TPC_STAGE_OUTPUT]
+ * the stages.  The counts are the work units the roofline figures are based on. */
+typedef struct {
+    float ms[8];
+    int kernel_launches;           /* kernels this library launched for the call */
+    int64_t clusters;              /* input clusters */
+    int64_t tracklets;             /* start hits = tracklets built (A4, A5) */
+    int64_t row_visits;            /* A5 row visits (searches), both passes */
+    int64_t candidates;            /* A5 clusters read inside the searched grid cells */
+    int64_t tracks;                /* output tracks */
+    int64_t hits;                  /* output clusters */
+} tpc_call_stats;
+
+/* Enable (1) or disable (0) per-stage event timing for the following calls. */
+int tpc_tracker_set_timing(tpc_tracker *tr, int enable);
+
+/* Fill *st for the call that produced res; waits for that call to finish.
+ * Errors: TPC_ERR_INVALID_ARG, TPC_ERR_CUDA. */
+int tpc_result_stats(tpc_result *res, tpc_call_stats *st);
+
+/* Intermediate buffers of the tracker's last call, for per-stage checks.  Device
+ * pointers into the tracker's workspace; valid until its next call.  Cluster
+ * slots are "sorted" positions: slot j of row unit u = (event * n_sectors +
+ * sector) * n_rows + row is sorted_offset[u] + j for j < count[u].  */
+typedef struct {
+    int64_t n_units;               /* events * n_sectors * n_rows */
+    int64_t n_slots;               /* size of the slot arrays */
+    int64_t n_tracklets;           /* tracklets (start hits) of the last call */
+    int64_t tracklet_capacity;
+    const int32_t *unit_meta;      /* [n_units * 4] input offset, count, sorted offset, cell offset */
+    const int32_t *unit_cells;     /* [n_units * 2] cells along y and z */
+    const float *unit_grid;        /* [n_units * 4] ymin, zmin, 1/dy, 1/dz */
+    const int32_t *cell_start;     /* cell starts, [cell offset + c], relative to the row's first slot */
+    const float *yz;               /* [n_slots * 2] y, z in slot order */
+    const int32_t *orig;           /* [n_slots] input index of each slot */
+    const int32_t *up_raw, *dn_raw;/* [n_slots] A2 links (slots, -1 none) */
+    const int32_t *up, *dn;        /* [n_slots] A3 kept links */
+    const int32_t *starts;         /* [n_tracklets * 4] first, middle, last slot, (sector << 16) | (chain length << 8) | row */
+    const int32_t *tl_nhits;       /* [capacity] */
+    const int32_t *tl_hits;        /* [capacity * n_rows] slots, outer to inner */
+    const float *tl_par;           /* [5 * capacity] component-major */
+    const float *tl_cov;           /* [15 * capacity] component-major */
+    const float *tl_x, *tl_chi2, *tl_w; /* [capacity] */
+    const int32_t *tl_nowned;      /* [capacity] */
+    const uint64_t *cluster_key;   /* [n_slots] winning weight key per slot */
+} tpc_debug_view;
+
+/* Fill *v from the tracker's last call (synchronises the device first). */
+int tpc_tracker_debug_view(tpc_tracker *tr, tpc_debug_view *v);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

@@ -100,6 +100,8 @@ def lib():
             L.orc_result_free.argtypes = [P]
             L.orc_seed_f64.restype = ctypes.c_int
             L.orc_seed_f64.argtypes = [P, P, P, ctypes.c_double, ctypes.c_double, P]
+            L.orc_asin_ratio_f32.restype = ctypes.c_float
+            L.orc_asin_ratio_f32.argtypes = [ctypes.c_float]
             L.orc_bin_row_f32.argtypes = [P, P, ctypes.c_int, ctypes.c_float, ctypes.c_float,
                                           ctypes.c_float, ctypes.c_float, ctypes.c_int, ctypes.c_int,
                                           P, P, P]
@@ -261,6 +263,11 @@ def seed(x3, y3, z3, bz=0.5, sin_max=0.99):
     st = np.zeros(5)
     ok = L.orc_seed_f64(x3.ctypes.data, y3.ctypes.data, z3.ctypes.data, float(bz), float(sin_max), st.ctypes.data)
     return bool(ok), st
+
+
+def asin_ratio_f32(u: float) -> float:
+    """asin(u)/u as evaluated by the float mode."""
+    return float(lib().orc_asin_ratio_f32(ctypes.c_float(u)))
 
 
 def bin_row(y, z, ymin, zmin, inv_dy, inv_dz, ny, nz):

@@ -105,6 +105,8 @@ void orc_bin_row_f32(const double *y, const double *z, int n, float ymin, float 
  * returns 0 when |sin phi| reaches sin_max. */
 int orc_propagate_f64(double *state, double *cov15, double x0, double x1, double bz, double sin_max);
 int orc_propagate_f32(double *state, double *cov15, double x0, double x1, double bz, double sin_max);
+/* asin(u)/u as the float mode evaluates it (series with half-angle reduction). */
+float orc_asin_ratio_f32(float u);
 /* Seed state from three (x, y, z) points (first, middle, last of a chain). */
 int orc_seed_f64(const double *x3, const double *y3, const double *z3, double bz, double sin_max,
                  double *state);

@@ -23,15 +23,47 @@
 #ifdef ORC_F32
 typedef float real;
 #define SQRT sqrtf
-#define ASIN asinf
 #define FABS fabsf
 #define SFX(name) name##_f32
 #else
 typedef double real;
 #define SQRT sqrt
-#define ASIN asin
 #define FABS fabs
 #define SFX(name) name##_f64
+#endif
+
+#ifdef ORC_F32
+/* asin(u)/u in float.  The float mode evaluates arcsin with a fixed series so that two
+ * float implementations of the tracker round identically (the weights of Section 3.1 decide
+ * cluster ownership by comparison).  Maclaurin series of arcsin,
+ *   asin(u)/u = sum_n (2n)! / (4^n (n!)^2 (2n+1)) u^(2n),
+ * twelve terms evaluated by Horner's rule for |u| <= 0.5 (truncation below 4e-10), after
+ * reducing larger |u| with the half-angle identity asin(u) = 2 asin(u / sqrt(2 (1 + sqrt(1 - u^2)))). */
+static float asin_ratio(float u)
+{
+    float v = u, m = 1.0f;
+    for (int k = 0; k < 3 && fabsf(v) > 0.5f; k++) {
+        v = v / sqrtf(2.0f * (1.0f + sqrtf(1.0f - v * v)));
+        m = m * 2.0f;
+    }
+    float t = v * v;
+    float s = 0.007312526f;                 /* 88179/12058624 */
+    s = s * t + 0.00839033537f;             /* 46189/5505024 */
+    s = s * t + 0.00976160914f;             /* 12155/1245184 */
+    s = s * t + 0.0115518011f;              /* 6435/557056 */
+    s = s * t + 0.0139648439f;              /* 143/10240 */
+    s = s * t + 0.0173527636f;              /* 231/13312 */
+    s = s * t + 0.0223721582f;              /* 63/2816 */
+    s = s * t + 0.030381944f;               /* 35/1152 */
+    s = s * t + 0.0446428582f;              /* 5/112 */
+    s = s * t + 0.075000003f;               /* 3/40 */
+    s = s * t + 0.166666672f;               /* 1/6 */
+    s = s * t + 1.0f;
+    if (m == 1.0f) return s;
+    return ((m * v) * s) / u;
+}
+#else
+static double asin_ratio(double u) { return (u != 0) ? asin(u) / u : 1.0; }
 #endif
 
 #define MAXB 4096            /* cap on grid cells per axis (the last cell absorbs the rest) */
@@ -216,7 +248,7 @@ static int propagate(KS *s, real x0, real x1, real kB, real smax)
     real L = SQRT(dx * dx + dy * dy);         /* chord, signed like dx */
     if (dx < 0) L = -L;
     real u = (cur * L) * (real)0.5;           /* sin of half the turning angle */
-    real ratio = (u != 0) ? ASIN(u) / u : (real)1;
+    real ratio = asin_ratio(u);
     real dS = L * ratio;                      /* arc length = 2 asin(C L / 2) / C */
     real tl = s->p[3];
     real dz = tl * dS;
@@ -321,7 +353,7 @@ static int seed3(const real *x, const real *y, const real *z, real kB, real smax
     real ca = SQRT((real)1 - sa * sa);
     real sinphi = (by / lb) * ca - (bx / lb) * sa;
     if (!(FABS(sinphi) < smax)) return 0;
-    real S02 = (sa != 0) ? lb * (ASIN(sa) / sa) : lb;
+    real S02 = lb * asin_ratio(sa);
     p[0] = y[0];
     p[1] = z[0];
     p[2] = sinphi;
@@ -739,6 +771,8 @@ int orc_seed_f64(const double *x3, const double *y3, const double *z3, double bz
 #endif
 
 #ifdef ORC_F32
+float orc_asin_ratio_f32(float u) { return asin_ratio(u); }
+
 void orc_bin_row_f32(const double *y, const double *z, int n, float ymin, float zmin, float inv_dy,
                      float inv_dz, int ny, int nz, int32_t *cell, int32_t *perm, int32_t *cell_start)
 {

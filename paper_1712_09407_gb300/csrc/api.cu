@@ -1,0 +1,742 @@
+// Host side of the C ABI declared in include/tpcca.h: tracker lifetime, device workspace,
+// per-call staging and the stage launches, results.
+#include <cmath>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <mutex>
+#include <new>
+#include <vector>
+
+#include "common.cuh"
+#include "../../include/tpcca.h"
+
+using namespace tpc;
+
+namespace {
+
+constexpr int kStaging = 4;             // ring of pinned staging buffers
+constexpr int kCountWords = CNT_COUNT + 4;
+
+struct Staging {
+    int4 *meta = nullptr;
+    int2 *dims = nullptr;
+    int64_t cap = 0;
+    cudaEvent_t consumed = nullptr;     // recorded after the H2D copy that reads this buffer
+    bool pending = false;
+};
+
+struct Alloc {
+    void *base = nullptr;
+    size_t bytes = 0;
+    size_t used = 0;
+    template <class T>
+    T *take(int64_t count)
+    {
+        size_t b = ((size_t)(count > 0 ? count : 1) * sizeof(T) + 255) & ~(size_t)255;
+        T *p = (T *)((char *)base + used);
+        used += b;
+        return p;
+    }
+};
+
+}  // namespace
+
+struct tpc_tracker {
+    int device = 0;
+    int num_sms = 0;
+    DevConst dc{};
+    tpc_params params{};
+    tpc_tuning tuning{};
+    int n_rows = 0, n_sectors = 0;
+    float row_x[kMaxRows + 1]{};
+    float tan_half = 0.0f, z_max = 0.0f;
+    size_t budget = 0;
+    size_t bytes_ws = 0, bytes_results = 0;
+    // workspace
+    void *ws_base = nullptr;
+    Workspace w{};
+    int64_t cap_n = -1, cap_units = -1;
+    // device copy of host inputs for tpc_track_event_host
+    void *in_base = nullptr;
+    int64_t in_cap = 0;
+    cudaEvent_t ws_done = nullptr;
+    bool ws_used = false;
+    Staging staging[kStaging];
+    int next_staging = 0;
+    std::vector<int4> meta;
+    std::vector<int2> dims;
+    // last call
+    int64_t last_units = 0, last_slots = 0, last_n = 0;
+    bool timing = false;
+    int last_err[4] = {0, 0, 0, 0};
+    std::mutex mu;
+};
+
+struct tpc_result {
+    tpc_tracker *tr = nullptr;
+    cudaStream_t stream = nullptr;
+    cudaEvent_t done = nullptr;
+    void *dev = nullptr;
+    size_t bytes = 0;
+    OutBuffers out{};
+    int32_t *h_counts = nullptr;        // pinned: counters then error word
+    bool synced = false;
+    int status = TPC_OK;
+    int64_t n_tracks = 0, n_hits = 0;
+    int64_t n_clusters = 0;
+    int launches = 0;
+    bool timed = false;
+    cudaEvent_t stage_ev[8] = {};
+};
+
+static int cuda_fail(cudaError_t e)
+{
+    if (e != cudaSuccess) {
+        fprintf(stderr, "tpcca: CUDA error %s\n", cudaGetErrorString(e));
+        return TPC_ERR_CUDA;
+    }
+    return TPC_OK;
+}
+
+#define TPC_CUDA(x)                                      \
+    do {                                                 \
+        int _s = cuda_fail(x);                           \
+        if (_s != TPC_OK) return _s;                     \
+    } while (0)
+
+extern "C" void tpc_params_default(tpc_params *p)
+{
+    if (!p) return;
+    p->sigma_y = 0.08f;
+    p->sigma_z = 0.1f;
+    p->nb_ty = 1.0f;
+    p->nb_tz = 2.0f;
+    p->nb_gate = 9.0f;
+    p->min_chain = 3;
+    p->seed_cov[0] = (float)(0.08 * 0.08);
+    p->seed_cov[1] = (float)(0.1 * 0.1);
+    p->seed_cov[2] = 0.01f;
+    p->seed_cov[3] = 0.01f;
+    p->seed_cov[4] = 1.0f;
+    p->win_nsigma = 3.0f;
+    p->chi2_max = 16.0f;
+    p->max_miss = 10;
+    p->edge_margin = 2.0f;
+    p->sin_max = 0.99f;
+    p->alpha = 6.0f;            // Section 3.1
+    p->beta = 1.0f;
+    p->min_clusters = 30;       // Section 5
+    p->qpt_max = 20.0f;
+}
+
+extern "C" void tpc_tuning_default(tpc_tuning *t)
+{
+    if (!t) return;
+    t->bin_occupancy = 2.0f;
+    t->neighbours_block = 128;
+    t->construct_block = 128;
+    t->construct_ctas_per_sm = 0;
+    t->stage_rows = 1;
+}
+
+extern "C" const char *tpc_status_string(int s)
+{
+    switch (s) {
+    case TPC_OK: return "ok";
+    case TPC_ERR_INVALID_ARG: return "invalid argument";
+    case TPC_ERR_CAPACITY: return "device pool capacity exceeded";
+    case TPC_ERR_BUDGET: return "HBM budget exceeded";
+    case TPC_ERR_TIMEOUT: return "bounded device wait expired";
+    case TPC_ERR_CUDA: return "CUDA runtime error";
+    case TPC_ERR_STATE: return "invalid call order";
+    default: return "unknown status";
+    }
+}
+
+static void fill_const(tpc_tracker *tr, float bz)
+{
+    DevConst &c = tr->dc;
+    const tpc_params &p = tr->params;
+    memset(&c, 0, sizeof c);
+    for (int r = 0; r < tr->n_rows; r++) c.row_x[r] = tr->row_x[r];
+    for (int s = 0; s < tr->n_sectors; s++)
+        c.sec_alpha[s] = (float)((20.0 * (s % 18) + 10.0) * M_PI / 180.0);
+    c.nr = tr->n_rows;
+    c.ns = tr->n_sectors;
+    c.th = tr->tan_half;
+    c.margin = p.edge_margin;
+    c.smax = p.sin_max;
+    c.sy2 = p.sigma_y * p.sigma_y;
+    c.sz2 = p.sigma_z * p.sigma_z;
+    c.isy2 = 1.0f / c.sy2;
+    c.isz2 = 1.0f / c.sz2;
+    c.ty = p.nb_ty;
+    c.tz = p.nb_tz;
+    c.gate9 = p.nb_gate;
+    for (int i = 0; i < 5; i++) c.cov0[i] = p.seed_cov[i];
+    c.nsig = p.win_nsigma;
+    c.chi2max = p.chi2_max;
+    c.alpha = p.alpha;
+    c.beta = p.beta;
+    c.qptmax = p.qpt_max;
+    c.kB = (float)(-2.99792458e-3 * (double)bz);
+    c.max_miss = p.max_miss;
+    c.min_chain = p.min_chain;
+    c.min_clusters = p.min_clusters;
+}
+
+extern "C" int tpc_tracker_create(const tpc_geometry *g, float bz, const tpc_params *params, size_t budget,
+                                  tpc_tracker **out)
+{
+    if (!out || !g || !g->row_x) return TPC_ERR_INVALID_ARG;
+    *out = nullptr;
+    if (g->n_rows < 3 || g->n_rows > kMaxRows) return TPC_ERR_INVALID_ARG;
+    if (g->n_sectors != 1 && g->n_sectors != 36) return TPC_ERR_INVALID_ARG;
+    for (int r = 1; r < g->n_rows; r++)
+        if (!(g->row_x[r] > g->row_x[r - 1])) return TPC_ERR_INVALID_ARG;
+    tpc_tracker *tr = new (std::nothrow) tpc_tracker();
+    if (!tr) return TPC_ERR_CUDA;
+    if (cudaGetDevice(&tr->device) != cudaSuccess ||
+        cudaDeviceGetAttribute(&tr->num_sms, cudaDevAttrMultiProcessorCount, tr->device) != cudaSuccess) {
+        delete tr;
+        return TPC_ERR_CUDA;
+    }
+    tr->n_rows = g->n_rows;
+    tr->n_sectors = g->n_sectors;
+    memcpy(tr->row_x, g->row_x, sizeof(float) * g->n_rows);
+    tr->tan_half = g->tan_half;
+    tr->z_max = g->z_max;
+    tr->budget = budget;
+    if (params)
+        tr->params = *params;
+    else
+        tpc_params_default(&tr->params);
+    tpc_tuning_default(&tr->tuning);
+    fill_const(tr, bz);
+    if (cudaEventCreateWithFlags(&tr->ws_done, cudaEventDisableTiming) != cudaSuccess) {
+        delete tr;
+        return TPC_ERR_CUDA;
+    }
+    for (auto &s : tr->staging) cudaEventCreateWithFlags(&s.consumed, cudaEventDisableTiming);
+    // keep freed result memory in the stream-ordered pool instead of returning it to the driver
+    cudaMemPool_t pool;
+    if (cudaDeviceGetDefaultMemPool(&pool, tr->device) == cudaSuccess) {
+        uint64_t thr = UINT64_MAX;
+        cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &thr);
+    }
+    *out = tr;
+    return TPC_OK;
+}
+
+extern "C" int tpc_tracker_set_tuning(tpc_tracker *tr, const tpc_tuning *t)
+{
+    if (!tr || !t) return TPC_ERR_INVALID_ARG;
+    if (!(t->bin_occupancy >= 0.5f) || t->neighbours_block < 32 || t->neighbours_block > 256 ||
+        t->neighbours_block % 32 || t->construct_block < 32 || t->construct_block > 256 ||
+        t->construct_block % 32 || t->construct_ctas_per_sm < 0)
+        return TPC_ERR_INVALID_ARG;
+    tr->tuning = *t;
+    return TPC_OK;
+}
+
+// Sizes of the workspace for n clusters in `events` events.
+struct WsSizes {
+    int64_t R, P, C, T, W;
+};
+
+static WsSizes ws_sizes(const tpc_tracker *tr, int64_t n, int64_t events)
+{
+    WsSizes s;
+    s.R = events * tr->n_sectors * tr->n_rows;
+    s.P = n + s.R * kSlotAlign + 64;
+    s.C = (int64_t)std::ceil((double)n / 0.5) + s.R * (kCellAlign + 1) + 64;
+    s.T = n / 4 + 64;
+    s.W = n / 32 + 4;
+    return s;
+}
+
+static size_t carve(tpc_tracker *tr, const WsSizes &s, Alloc &a)
+{
+    Workspace &w = tr->w;
+    w.meta = a.take<int4>(s.R);
+    w.dims = a.take<int2>(s.R);
+    w.grid = a.take<float4>(s.R);
+    w.cell = a.take<int32_t>(s.C);
+    w.yz = a.take<float2>(s.P);
+    w.orig = a.take<int32_t>(s.P);
+    w.up_raw = a.take<int32_t>(s.P);
+    w.dn_raw = a.take<int32_t>(s.P);
+    w.up = a.take<int32_t>(s.P);
+    w.dn = a.take<int32_t>(s.P);
+    w.ckey = a.take<unsigned long long>(s.P);
+    w.starts = a.take<int4>(s.T);
+    w.tl_n = a.take<int32_t>(s.T);
+    w.tl_hits = a.take<int32_t>(s.T * tr->n_rows);
+    w.tl_par = a.take<float>(5 * s.T);
+    w.tl_cov = a.take<float>(15 * s.T);
+    w.tl_x = a.take<float>(s.T);
+    w.tl_chi2 = a.take<float>(s.T);
+    w.tl_w = a.take<float>(s.T);
+    w.tl_key = a.take<unsigned long long>(s.T);
+    w.tl_nowned = a.take<int32_t>(s.T);
+    w.tl_inner = a.take<int32_t>(s.T);
+    w.bits = a.take<uint32_t>(s.W);
+    w.word_off = a.take<int32_t>(s.W);
+    w.rank_trk = a.take<int32_t>(s.T);
+    w.rank_first = a.take<int32_t>(s.T);
+    w.scan_tmp = a.take<int32_t>((s.W > s.T ? s.W : s.T) / 4096 + 64);
+    w.counters = a.take<int32_t>(kCountWords);
+    w.err = w.counters + CNT_COUNT;
+    w.ncap = s.P;
+    w.pcap = s.P;
+    w.ccap = s.C;
+    w.tcap = s.T;
+    w.rcap = s.R;
+    w.wcap = s.W;
+    return a.used;
+}
+
+static int reserve(tpc_tracker *tr, int64_t n, int64_t events)
+{
+    if (n <= tr->cap_n && events <= tr->cap_units) return TPC_OK;
+    int64_t nn = n > tr->cap_n ? n : tr->cap_n;
+    int64_t ee = events > tr->cap_units ? events : tr->cap_units;
+    if (nn < 1024) nn = 1024;
+    if (ee < 1) ee = 1;
+    WsSizes s = ws_sizes(tr, nn, ee);
+    Alloc probe;              // dry run on a null base to get the size
+    Workspace keep = tr->w;
+    size_t need = carve(tr, s, probe);
+    tr->w = keep;
+    if (tr->budget && need + tr->bytes_results > tr->budget) return TPC_ERR_BUDGET;
+    if (tr->ws_base) {
+        TPC_CUDA(cudaDeviceSynchronize());
+        cudaFree(tr->ws_base);
+        tr->ws_base = nullptr;
+        tr->bytes_ws = 0;
+    }
+    TPC_CUDA(cudaMalloc(&tr->ws_base, need));
+    Alloc a;
+    a.base = tr->ws_base;
+    a.bytes = need;
+    carve(tr, s, a);
+    tr->bytes_ws = need;
+    tr->cap_n = nn;
+    tr->cap_units = ee;
+    return TPC_OK;
+}
+
+extern "C" int tpc_tracker_reserve(tpc_tracker *tr, int64_t max_clusters, int max_events)
+{
+    if (!tr || max_clusters < 0 || max_events < 1) return TPC_ERR_INVALID_ARG;
+    return reserve(tr, max_clusters, max_events);
+}
+
+static size_t result_bytes(int64_t tcap, int64_t ncap)
+{
+    size_t b = 0;
+    auto add = [&](size_t x) { b += (x + 255) & ~(size_t)255; };
+    add(tcap * 5 * 4);
+    add(tcap * 15 * 4);
+    for (int i = 0; i < 3; i++) add(tcap * 4);
+    for (int i = 0; i < 5; i++) add(tcap * 4);
+    add((ncap > 0 ? ncap : 1) * 4);
+    return b;
+}
+
+static void carve_result(tpc_result *r, int64_t tcap, int64_t ncap)
+{
+    Alloc a;
+    a.base = r->dev;
+    r->out.par = a.take<float>(tcap * 5);
+    r->out.cov = a.take<float>(tcap * 15);
+    r->out.x = a.take<float>(tcap);
+    r->out.alpha = a.take<float>(tcap);
+    r->out.chi2 = a.take<float>(tcap);
+    r->out.ndf = a.take<int32_t>(tcap);
+    r->out.nhits = a.take<int32_t>(tcap);
+    r->out.first = a.take<int32_t>(tcap);
+    r->out.sector = a.take<int32_t>(tcap);
+    r->out.event = a.take<int32_t>(tcap);
+    r->out.hits = a.take<int32_t>(ncap > 0 ? ncap : 1);
+}
+
+static int run(tpc_tracker *tr, const float *y, const float *z, const uint8_t *row, const int32_t *counts,
+               int n_events, int64_t n_total, cudaStream_t st, tpc_result **out)
+{
+    const int nr = tr->n_rows, ns = tr->n_sectors;
+    const int64_t R = (int64_t)n_events * ns * nr;
+    // host validation of counts
+    int64_t sum = 0;
+    for (int64_t u = 0; u < R; u++) {
+        if (counts[u] < 0) return TPC_ERR_INVALID_ARG;
+        sum += counts[u];
+    }
+    if (sum != n_total || n_total > INT32_MAX / 2) return TPC_ERR_INVALID_ARG;
+    if ((int64_t)n_events * ns >= (1 << 15)) return TPC_ERR_INVALID_ARG;   // sector index packs into 15 bits
+    if (n_total > 0 && (!y || !z || !row)) return TPC_ERR_INVALID_ARG;
+    int s = reserve(tr, n_total, n_events);
+    if (s != TPC_OK) return s;
+    // result memory
+    tpc_result *res = new (std::nothrow) tpc_result();
+    if (!res) return TPC_ERR_CUDA;
+    res->tr = tr;
+    res->stream = st;
+    const int64_t tcap = tr->w.tcap;
+    const int64_t hcap = n_total;
+    res->bytes = result_bytes(tcap, hcap);
+    if (tr->budget && tr->bytes_ws + tr->bytes_results + res->bytes > tr->budget) {
+        delete res;
+        return TPC_ERR_BUDGET;
+    }
+    if (cudaMallocAsync(&res->dev, res->bytes, st) != cudaSuccess ||
+        cudaMallocHost((void **)&res->h_counts, kCountWords * sizeof(int32_t)) != cudaSuccess ||
+        cudaEventCreateWithFlags(&res->done, cudaEventDisableTiming) != cudaSuccess) {
+        if (res->dev) cudaFreeAsync(res->dev, st);
+        if (res->h_counts) cudaFreeHost(res->h_counts);
+        delete res;
+        return TPC_ERR_CUDA;
+    }
+    tr->bytes_results += res->bytes;
+    carve_result(res, tcap, hcap);
+
+    // per row unit metadata
+    tr->meta.resize(R);
+    tr->dims.resize(R);
+    int64_t in_off = 0, s_off = 0, c_off = 0;
+    int smem_need = 0;
+    const float occ = tr->tuning.bin_occupancy;
+    for (int64_t u = 0; u < R; u++) {
+        const int n = counts[u];
+        const int r = (int)(u % nr);
+        int ncell = (int)std::ceil((double)n / occ);
+        if (ncell < 1) ncell = 1;
+        if (ncell > kCellMax) ncell = kCellMax;
+        const double wy = 2.0 * tr->row_x[r] * tr->tan_half;
+        const double wz = (ns == 36 ? 1.0 : 2.0) * tr->z_max;
+        int ny = (int)std::lround(std::sqrt(ncell * wy / wz));
+        if (ny < 1) ny = 1;
+        if (ny > ncell) ny = ncell;
+        int nz = ncell / ny;
+        if (nz < 1) nz = 1;
+        tr->meta[u] = make_int4((int)in_off, n, (int)s_off, (int)c_off);
+        tr->dims[u] = make_int2(ny, nz);
+        in_off += n;
+        s_off += (n + kSlotAlign - 1) / kSlotAlign * kSlotAlign;
+        c_off += (ny * nz + 1 + kCellAlign - 1) / kCellAlign * kCellAlign;
+    }
+    for (int64_t u = 0; u < R; u++) {
+        const int r = (int)(u % nr);
+        if (r == 0 || r == nr - 1) continue;
+        const int4 a = tr->meta[u + 1], b = tr->meta[u - 1];
+        const int2 da = tr->dims[u + 1], db = tr->dims[u - 1];
+        auto rb = [](int n, int nc) {
+            auto r16 = [](int x) { return (x + 15) & ~15; };
+            return r16(n * 8) + r16(n * 4) + r16((nc + 1) * 4);
+        };
+        const int bytes = rb(a.y, da.x * da.y) + rb(b.y, db.x * db.y);
+        if (bytes > smem_need) smem_need = bytes;
+    }
+    if (s_off + 64 > tr->w.pcap || c_off + 64 > tr->w.ccap) {
+        // cannot happen with ws_sizes' bounds; guard anyway
+        tr->bytes_results -= res->bytes;
+        cudaFreeAsync(res->dev, st);
+        cudaFreeHost(res->h_counts);
+        cudaEventDestroy(res->done);
+        delete res;
+        return TPC_ERR_CAPACITY;
+    }
+    int smem = smem_need < neighbours_smem_limit() ? smem_need : neighbours_smem_limit();
+
+    Staging &sg = tr->staging[tr->next_staging];
+    tr->next_staging = (tr->next_staging + 1) % kStaging;
+    if (sg.pending) {
+        TPC_CUDA(cudaEventSynchronize(sg.consumed));
+        sg.pending = false;
+    }
+    if (sg.cap < R) {
+        if (sg.meta) cudaFreeHost(sg.meta);
+        if (sg.dims) cudaFreeHost(sg.dims);
+        sg.meta = nullptr;
+        sg.dims = nullptr;
+        int64_t cap = R < 1 ? 1 : R;
+        TPC_CUDA(cudaMallocHost((void **)&sg.meta, cap * sizeof(int4)));
+        TPC_CUDA(cudaMallocHost((void **)&sg.dims, cap * sizeof(int2)));
+        sg.cap = cap;
+    }
+    memcpy(sg.meta, tr->meta.data(), R * sizeof(int4));
+    memcpy(sg.dims, tr->dims.data(), R * sizeof(int2));
+
+    if (tr->ws_used) TPC_CUDA(cudaStreamWaitEvent(st, tr->ws_done, 0));
+    const bool timed = tr->timing;
+    if (timed) {
+        for (auto &e : res->stage_ev) TPC_CUDA(cudaEventCreate(&e));
+        TPC_CUDA(cudaEventRecord(res->stage_ev[0], st));
+    }
+    res->timed = timed;
+    res->n_clusters = n_total;
+    const Workspace &w = tr->w;
+    if (R > 0) {
+        TPC_CUDA(cudaMemcpyAsync(w.meta, sg.meta, R * sizeof(int4), cudaMemcpyHostToDevice, st));
+        TPC_CUDA(cudaMemcpyAsync(w.dims, sg.dims, R * sizeof(int2), cudaMemcpyHostToDevice, st));
+    }
+    TPC_CUDA(cudaEventRecord(sg.consumed, st));
+    sg.pending = true;
+    TPC_CUDA(cudaMemsetAsync(w.counters, 0, kCountWords * sizeof(int32_t), st));
+    TPC_CUDA(cudaMemsetAsync(w.bits, 0, ((n_total + 31) / 32 + 2) * sizeof(uint32_t), st));
+    TPC_CUDA(cudaMemsetAsync(w.ckey, 0, s_off * sizeof(unsigned long long), st));
+
+    LaunchCfg lc;
+    lc.num_sms = tr->num_sms;
+    lc.neighbours_block = tr->tuning.neighbours_block;
+    lc.construct_block = tr->tuning.construct_block;
+    lc.construct_ctas_per_sm = tr->tuning.construct_ctas_per_sm;
+    lc.stage_rows = tr->tuning.stage_rows;
+    lc.neighbours_smem_max = smem;
+
+    int launches = 0;
+    auto mark = [&](int i) {
+        if (timed) cudaEventRecord(res->stage_ev[i], st);
+    };
+    mark(1);
+    launches += launch_ingest(tr->dc, w, y, z, row, R, st);
+    mark(2);
+    launches += launch_neighbours(tr->dc, w, R, smem, lc, st);
+    mark(3);
+    launches += launch_evolve(tr->dc, w, R, st);
+    mark(4);
+    launches += launch_construct(tr->dc, w, lc, st);
+    mark(5);
+    launches += launch_select(tr->dc, w, n_total, lc, st);
+    mark(6);
+    launches += launch_output(tr->dc, w, res->out, n_total, lc, st);
+    mark(7);
+    TPC_CUDA(cudaGetLastError());
+    res->launches = launches;
+    TPC_CUDA(cudaMemcpyAsync(res->h_counts, w.counters, kCountWords * sizeof(int32_t), cudaMemcpyDeviceToHost, st));
+    TPC_CUDA(cudaEventRecord(res->done, st));
+    TPC_CUDA(cudaEventRecord(tr->ws_done, st));
+    tr->ws_used = true;
+    tr->last_units = R;
+    tr->last_slots = s_off;
+    tr->last_n = n_total;
+    *out = res;
+    return TPC_OK;
+}
+
+extern "C" int tpc_track_batch(tpc_tracker *tr, const float *y, const float *z, const uint8_t *row,
+                               const int32_t *counts, int n_events, int64_t n_total, void *stream,
+                               tpc_result **out)
+{
+    if (!tr || !out || !counts || n_events < 1 || n_total < 0) return TPC_ERR_INVALID_ARG;
+    *out = nullptr;
+    std::lock_guard<std::mutex> g(tr->mu);
+    return run(tr, y, z, row, counts, n_events, n_total, (cudaStream_t)stream, out);
+}
+
+extern "C" int tpc_track_event(tpc_tracker *tr, const float *y, const float *z, const uint8_t *row,
+                               const int32_t *counts, int64_t n, void *stream, tpc_result **out)
+{
+    return tpc_track_batch(tr, y, z, row, counts, 1, n, stream, out);
+}
+
+extern "C" int tpc_track_event_host(tpc_tracker *tr, const float *y, const float *z, const uint8_t *row,
+                                    const int32_t *counts, int64_t n, void *stream, tpc_result **out)
+{
+    if (!tr || !out || !counts || n < 0) return TPC_ERR_INVALID_ARG;
+    if (n > 0 && (!y || !z || !row)) return TPC_ERR_INVALID_ARG;
+    *out = nullptr;
+    std::lock_guard<std::mutex> g(tr->mu);
+    cudaStream_t st = (cudaStream_t)stream;
+    if (n > tr->in_cap) {
+        if (tr->in_base) {
+            TPC_CUDA(cudaDeviceSynchronize());
+            cudaFree(tr->in_base);
+            tr->bytes_ws -= (size_t)tr->in_cap * 12;
+            tr->in_base = nullptr;
+        }
+        size_t need = (size_t)n * 12 + 1024;
+        if (tr->budget && tr->bytes_ws + tr->bytes_results + need > tr->budget) return TPC_ERR_BUDGET;
+        TPC_CUDA(cudaMalloc(&tr->in_base, need));
+        tr->in_cap = n;
+        tr->bytes_ws += (size_t)n * 12;
+    }
+    float *dy = (float *)tr->in_base;
+    float *dz = dy + tr->in_cap;
+    uint8_t *dr = (uint8_t *)(dz + tr->in_cap);
+    if (tr->ws_used) TPC_CUDA(cudaStreamWaitEvent(st, tr->ws_done, 0));
+    if (n > 0) {
+        TPC_CUDA(cudaMemcpyAsync(dy, y, n * sizeof(float), cudaMemcpyHostToDevice, st));
+        TPC_CUDA(cudaMemcpyAsync(dz, z, n * sizeof(float), cudaMemcpyHostToDevice, st));
+        TPC_CUDA(cudaMemcpyAsync(dr, row, n, cudaMemcpyHostToDevice, st));
+    }
+    return run(tr, dy, dz, dr, counts, 1, n, st, out);
+}
+
+extern "C" int tpc_result_sync_counts(tpc_result *r, int64_t *n_tracks, int64_t *n_hits)
+{
+    if (!r) return TPC_ERR_INVALID_ARG;
+    if (!r->synced) {
+        TPC_CUDA(cudaEventSynchronize(r->done));
+        r->synced = true;
+        const int32_t *err = r->h_counts + CNT_COUNT;
+        r->status = err[ERR_STATUS];
+        r->n_tracks = r->h_counts[CNT_TRACKS];
+        r->n_hits = r->h_counts[CNT_HITS];
+        if (r->status != TPC_OK) {
+            std::lock_guard<std::mutex> g(r->tr->mu);
+            memcpy(r->tr->last_err, err, sizeof(r->tr->last_err));
+        }
+    }
+    if (n_tracks) *n_tracks = r->n_tracks;
+    if (n_hits) *n_hits = r->n_hits;
+    return r->status;
+}
+
+extern "C" int tpc_result_get(tpc_result *r, tpc_track_view *v)
+{
+    if (!r || !v) return TPC_ERR_INVALID_ARG;
+    if (!r->synced) return TPC_ERR_STATE;
+    v->n_tracks = r->n_tracks;
+    v->n_hits = r->n_hits;
+    v->par = r->out.par;
+    v->cov = r->out.cov;
+    v->x_ref = r->out.x;
+    v->alpha = r->out.alpha;
+    v->chi2 = r->out.chi2;
+    v->ndf = r->out.ndf;
+    v->nhits = r->out.nhits;
+    v->first = r->out.first;
+    v->sector = r->out.sector;
+    v->event = r->out.event;
+    v->hits = r->out.hits;
+    return TPC_OK;
+}
+
+extern "C" int tpc_result_copy_to_host(tpc_result *r, float *par, float *cov, float *x_ref, float *alpha,
+                                       float *chi2, int32_t *ndf, int32_t *nhits, int32_t *first, int32_t *sector,
+                                       int32_t *event, int32_t *hits)
+{
+    if (!r) return TPC_ERR_INVALID_ARG;
+    int s = tpc_result_sync_counts(r, nullptr, nullptr);
+    if (s != TPC_OK) return s;
+    const int64_t M = r->n_tracks, H = r->n_hits;
+    cudaStream_t st = r->stream;
+    struct Item {
+        void *dst;
+        const void *src;
+        size_t bytes;
+    } items[] = {
+        {par, r->out.par, (size_t)M * 5 * 4}, {cov, r->out.cov, (size_t)M * 15 * 4}, {x_ref, r->out.x, (size_t)M * 4},
+        {alpha, r->out.alpha, (size_t)M * 4}, {chi2, r->out.chi2, (size_t)M * 4},    {ndf, r->out.ndf, (size_t)M * 4},
+        {nhits, r->out.nhits, (size_t)M * 4}, {first, r->out.first, (size_t)M * 4},  {sector, r->out.sector, (size_t)M * 4},
+        {event, r->out.event, (size_t)M * 4}, {hits, r->out.hits, (size_t)H * 4},
+    };
+    for (auto &it : items)
+        if (it.dst && it.bytes) TPC_CUDA(cudaMemcpyAsync(it.dst, it.src, it.bytes, cudaMemcpyDeviceToHost, st));
+    TPC_CUDA(cudaStreamSynchronize(st));
+    return TPC_OK;
+}
+
+extern "C" void tpc_result_release(tpc_result *r)
+{
+    if (!r) return;
+    if (r->dev) cudaFreeAsync(r->dev, r->stream);
+    if (r->done) {
+        cudaEventSynchronize(r->done);
+        cudaEventDestroy(r->done);
+    }
+    if (r->h_counts) cudaFreeHost(r->h_counts);
+    for (auto &e : r->stage_ev)
+        if (e) cudaEventDestroy(e);
+    {
+        std::lock_guard<std::mutex> g(r->tr->mu);
+        r->tr->bytes_results -= r->bytes;
+    }
+    delete r;
+}
+
+extern "C" void tpc_tracker_destroy(tpc_tracker *tr)
+{
+    if (!tr) return;
+    cudaDeviceSynchronize();
+    if (tr->ws_base) cudaFree(tr->ws_base);
+    if (tr->in_base) cudaFree(tr->in_base);
+    for (auto &s : tr->staging) {
+        if (s.meta) cudaFreeHost(s.meta);
+        if (s.dims) cudaFreeHost(s.dims);
+        if (s.consumed) cudaEventDestroy(s.consumed);
+    }
+    if (tr->ws_done) cudaEventDestroy(tr->ws_done);
+    delete tr;
+}
+
+extern "C" int tpc_last_error_detail(tpc_tracker *tr, int *event, int *sector, int *stage)
+{
+    if (!tr) return TPC_ERR_INVALID_ARG;
+    std::lock_guard<std::mutex> g(tr->mu);
+    if (event) *event = tr->last_err[ERR_EVENT];
+    if (sector) *sector = tr->last_err[ERR_SECTOR];
+    if (stage) *stage = tr->last_err[ERR_STAGE];
+    return tr->last_err[ERR_STATUS];
+}
+
+extern "C" int tpc_tracker_set_timing(tpc_tracker *tr, int enable)
+{
+    if (!tr) return TPC_ERR_INVALID_ARG;
+    tr->timing = enable != 0;
+    return TPC_OK;
+}
+
+extern "C" int tpc_result_stats(tpc_result *r, tpc_call_stats *st)
+{
+    if (!r || !st) return TPC_ERR_INVALID_ARG;
+    TPC_CUDA(cudaEventSynchronize(r->done));
+    memset(st, 0, sizeof *st);
+    if (r->timed)
+        for (int i = 0; i < 7; i++) TPC_CUDA(cudaEventElapsedTime(&st->ms[i], r->stage_ev[i], r->stage_ev[i + 1]));
+    st->kernel_launches = r->launches;
+    st->clusters = r->n_clusters;
+    st->tracklets = r->h_counts[CNT_STARTS];
+    st->row_visits = r->h_counts[CNT_VISITS];
+    st->candidates = r->h_counts[CNT_CANDS];
+    st->tracks = r->h_counts[CNT_TRACKS];
+    st->hits = r->h_counts[CNT_HITS];
+    return TPC_OK;
+}
+
+extern "C" int tpc_tracker_debug_view(tpc_tracker *tr, tpc_debug_view *v)
+{
+    if (!tr || !v) return TPC_ERR_INVALID_ARG;
+    if (!tr->ws_used) return TPC_ERR_STATE;
+    TPC_CUDA(cudaDeviceSynchronize());
+    int32_t cnt[CNT_COUNT];
+    TPC_CUDA(cudaMemcpy(cnt, tr->w.counters, sizeof cnt, cudaMemcpyDeviceToHost));
+    const Workspace &w = tr->w;
+    v->n_units = tr->last_units;
+    v->n_slots = tr->last_slots;
+    v->n_tracklets = cnt[CNT_STARTS] < w.tcap ? cnt[CNT_STARTS] : w.tcap;
+    v->tracklet_capacity = w.tcap;
+    v->unit_meta = (const int32_t *)w.meta;
+    v->unit_cells = (const int32_t *)w.dims;
+    v->unit_grid = (const float *)w.grid;
+    v->cell_start = w.cell;
+    v->yz = (const float *)w.yz;
+    v->orig = w.orig;
+    v->up_raw = w.up_raw;
+    v->dn_raw = w.dn_raw;
+    v->up = w.up;
+    v->dn = w.dn;
+    v->starts = (const int32_t *)w.starts;
+    v->tl_nhits = w.tl_n;
+    v->tl_hits = w.tl_hits;
+    v->tl_par = w.tl_par;
+    v->tl_cov = w.tl_cov;
+    v->tl_x = w.tl_x;
+    v->tl_chi2 = w.tl_chi2;
+    v->tl_w = w.tl_w;
+    v->tl_nowned = w.tl_nowned;
+    v->cluster_key = (const uint64_t *)w.ckey;
+    return TPC_OK;
+}

@@ -1,0 +1,166 @@
+// Internal definitions shared by the kernels and the host side of the tracker library.
+#pragma once
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace tpc {
+
+constexpr int kMaxRows = 255;       // row index is a uint8
+constexpr int kMaxSectors = 36;
+constexpr int kCellMax = 1024;      // grid cells per row unit (host clamps)
+constexpr int kSlotAlign = 8;       // sorted row segments start on 8-element (32 B) boundaries
+constexpr int kCellAlign = 4;       // cell-start segments start on 16 B boundaries
+constexpr unsigned kFull = 0xffffffffu;
+
+// Error word layout in the workspace: [0] status, [1] event, [2] sector, [3] stage.
+enum { ERR_STATUS = 0, ERR_EVENT = 1, ERR_SECTOR = 2, ERR_STAGE = 3 };
+
+// Counters in the workspace.
+enum {
+    CNT_STARTS = 0,     // tracklets found by A4
+    CNT_QUEUE = 1,      // A5 work-queue head
+    CNT_TRACKS = 2,     // accepted tracks (A7)
+    CNT_HITS = 3,       // output hits (A7)
+    CNT_VISITS = 4,     // A5 row visits (statistics)
+    CNT_CANDS = 5,      // A5 clusters read inside the enumerated grid cells (statistics)
+    CNT_COUNT = 8
+};
+
+// Constants of one tracker, passed by value to every kernel (kernel parameter space).
+struct DevConst {
+    float row_x[kMaxRows + 1];
+    float sec_alpha[kMaxSectors];
+    int nr;             // rows
+    int ns;             // sectors per event
+    float th;           // tan of the sector half-opening
+    float margin;       // edge margin of the construction
+    float smax;         // |sin phi| limit
+    float sy2, sz2;     // sigma_y^2, sigma_z^2
+    float isy2, isz2;   // 1 / sigma^2
+    float ty, tz;       // neighbours window slopes
+    float gate9;        // neighbours gate factor
+    float cov0[5];      // seed covariance diagonal
+    float nsig;         // search window in sigmas
+    float chi2max;      // cluster gate
+    float alpha, beta;  // cluster weight constants
+    float qptmax;       // low-momentum cut
+    float kB;           // curvature per unit q/pT: -kappa * Bz
+    int max_miss;
+    int min_chain;
+    int min_clusters;
+};
+
+// Per row unit metadata (host-computed): input offset, count, sorted offset, cell offset.
+// A row unit is one pad row of one sector of one event: u = (event * ns + sector) * nr + row.
+struct Workspace {
+    // per row unit
+    int4 *meta;            // {in_off, n, s_off, cell_off}
+    int2 *dims;            // {ny, nz}
+    float4 *grid;          // {ymin, zmin, 1/dy, 1/dz}
+    int32_t *cell;         // cell starts relative to the row's first slot
+    // per cluster slot (sorted order, padded per row unit)
+    float2 *yz;
+    int32_t *orig;
+    int32_t *up_raw, *dn_raw, *up, *dn;
+    unsigned long long *ckey;   // A6 claims
+    // per tracklet
+    int4 *starts;          // {first, mid, last, (sector << 16) | (chain length << 8) | row}
+    int32_t *tl_n;
+    int32_t *tl_hits;      // [tcap * nr]
+    float *tl_par;         // [5 * tcap]
+    float *tl_cov;         // [15 * tcap]
+    float *tl_x, *tl_chi2, *tl_w;
+    unsigned long long *tl_key;
+    int32_t *tl_nowned;
+    int32_t *tl_inner;     // input index of the innermost owned cluster, -1 if rejected
+    // output ordering
+    uint32_t *bits;        // bitmap over input indices of innermost clusters
+    int32_t *word_off;     // exclusive prefix of popcounts
+    int32_t *rank_trk;     // tracklet of each output rank
+    int32_t *rank_first;   // hit offset of each output rank
+    int32_t *scan_tmp;     // scratch for block partials
+    int32_t *counters;     // [CNT_COUNT]
+    int32_t *err;          // [4]
+    int64_t ncap, pcap, ccap, tcap, rcap, wcap;
+};
+
+struct OutBuffers {
+    float *par, *cov, *x, *alpha, *chi2;
+    int32_t *ndf, *nhits, *first, *sector, *event, *hits;
+};
+
+// --------------------------------------------------------------------------------------------
+// device helpers
+// --------------------------------------------------------------------------------------------
+__device__ __forceinline__ void set_error(int32_t *err, int status, int unit, const DevConst &c, int stage)
+{
+    if (atomicCAS(&err[ERR_STATUS], 0, status) == 0) {
+        int sec = unit / c.nr;
+        err[ERR_EVENT] = sec / c.ns;
+        err[ERR_SECTOR] = sec % c.ns;
+        err[ERR_STAGE] = stage;
+    }
+}
+
+// Monotone map of a float to an unsigned integer (larger float -> larger integer).
+__device__ __forceinline__ uint32_t ordered_bits(float f)
+{
+    uint32_t b = __float_as_uint(f);
+    return (b & 0x80000000u) ? ~b : (b | 0x80000000u);
+}
+
+// Grid cell along one axis; monotone non-decreasing in v.
+__device__ __forceinline__ int cell1(float v, float vmin, float inv, int nb)
+{
+    float t = (v - vmin) * inv;
+    if (!(t >= 0.0f)) return 0;
+    if (t >= (float)nb) return nb - 1;
+    return (int)t;
+}
+
+__device__ __forceinline__ unsigned lanemask_lt()
+{
+    unsigned m;
+    asm("mov.u32 %0, %%lanemask_lt;" : "=r"(m));
+    return m;
+}
+
+// Inclusive warp scan.
+__device__ __forceinline__ int warp_incl_scan(int v)
+{
+    int lane = threadIdx.x & 31;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        int t = __shfl_up_sync(kFull, v, o);
+        if (lane >= o) v += t;
+    }
+    return v;
+}
+
+// Bin range slack: windows are widened by this much (cm) before the cell lookup so
+// that rounding can never hide a cluster that passes the exact window test.
+constexpr float kBinSlack = 1e-3f;
+
+}  // namespace tpc
+
+// Launchers (host side), one per stage; defined next to their kernels.
+namespace tpc {
+struct LaunchCfg {
+    int num_sms;
+    int neighbours_block;
+    int construct_block;
+    int construct_ctas_per_sm;
+    int stage_rows;
+    int neighbours_smem_max;   // bytes of dynamic shared memory for staged rows
+};
+int launch_ingest(const DevConst &c, const Workspace &w, const float *y, const float *z, const uint8_t *row,
+                   int64_t R, cudaStream_t s);
+int launch_neighbours(const DevConst &c, const Workspace &w, int64_t R, int smem_bytes, const LaunchCfg &lc,
+                       cudaStream_t s);
+int launch_evolve(const DevConst &c, const Workspace &w, int64_t R, cudaStream_t s);
+int launch_construct(const DevConst &c, const Workspace &w, const LaunchCfg &lc, cudaStream_t s);
+int launch_select(const DevConst &c, const Workspace &w, int64_t n_input, const LaunchCfg &lc, cudaStream_t s);
+int launch_output(const DevConst &c, const Workspace &w, const OutBuffers &o, int64_t n_input,
+                   const LaunchCfg &lc, cudaStream_t s);
+int neighbours_smem_limit();
+}  // namespace tpc

@@ -1,0 +1,330 @@
+"""Parity of the CUDA tracker (through the C ABI) with the float-mode CPU oracle, stage by stage.
+
+Tolerances (the spec contract of the build): link agreement and track-by-track,
+cluster-by-cluster concordance >= 99.99 %; parameters of matched tracks within 1e-4
+relative (denominators max(|ref|, scale) with scales 1 cm, 1 cm, 1e-3, 1e-3, 1e-2 e/GeV);
+exact cluster lists for matched tracks.  Integer stages (binning, cell starts) must be
+bit-exact.  The float expressions of both sides are evaluated in the same order without
+contraction, so in practice the comparison is exact except where asinf rounds differently.
+"""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from paper_1712_09407_gb300 import concordance, eventgen
+from paper_1712_09407_gb300.tracker import Tracker, TrackerError
+
+from gpu_util import (compare_tracks, links_as_input_indices, owners_by_start, run_gpu, run_oracle, to_device,
+                      tracklets_by_start, valid_slots)
+
+pytestmark = pytest.mark.gpu
+
+CONCORDANCE_MIN = 0.9999
+PAR_REL = 1e-4
+
+
+@pytest.fixture(scope="module")
+def ev1():
+    return eventgen.config_event(1)
+
+
+@pytest.fixture(scope="module")
+def ev0():
+    return eventgen.config_event(0)
+
+
+def _small36():
+    spec = eventgen.EventSpec(n_primaries=600, n_secondaries=100, pt_cut=0.05, noise_frac=0.2)
+    return eventgen.generate_event(spec, eventgen.Geometry(), seed=5)
+
+
+# ---------------------------------------------------------------------------------------------
+# A1
+# ---------------------------------------------------------------------------------------------
+@pytest.mark.parametrize("which", ["c0", "small36"])
+def test_a1_binning_bit_exact(which, ev0):
+    ev = ev0 if which == "c0" else _small36()
+    tr, out, dbg = run_gpu(ev)
+    meta = dbg["meta"].cpu().numpy()
+    cells = dbg["cells"].cpu().numpy()
+    grid = dbg["grid"].cpu().numpy()
+    cs = dbg["cell_start"].cpu().numpy()
+    orig = dbg["orig"].cpu().numpy()
+    yz = dbg["yz"].cpu().numpy()
+    checked = 0
+    for u in range(meta.shape[0]):
+        in_off, n, s_off, c_off = meta[u]
+        if n == 0:
+            continue
+        ny, nz = cells[u]
+        yy, zz = ev.y[in_off:in_off + n], ev.z[in_off:in_off + n]
+        assert grid[u, 0] == yy.min() and grid[u, 1] == zz.min()
+        cell, perm, cstart = oracle.bin_row(yy, zz, grid[u, 0], grid[u, 1], grid[u, 2], grid[u, 3], ny, nz)
+        assert np.array_equal(orig[s_off:s_off + n], in_off + perm), u
+        assert np.array_equal(cs[c_off:c_off + ny * nz + 1], cstart), u
+        assert np.array_equal(yz[s_off:s_off + n, 0], yy[perm]) and np.array_equal(yz[s_off:s_off + n, 1], zz[perm])
+        checked += 1
+    assert checked > 0
+    tr.close()
+
+
+# ---------------------------------------------------------------------------------------------
+# A2 .. A6 on one event
+# ---------------------------------------------------------------------------------------------
+@pytest.fixture(scope="module")
+def both1(ev1):
+    tr, out, dbg = run_gpu(ev1)
+    ref = run_oracle(ev1, key="c1")
+    tr.close()
+    return ev1, out, dbg, ref
+
+
+def test_a2_a3_links(both1):
+    ev, out, dbg, ref = both1
+    L = links_as_input_indices(dbg, ev.n)
+    for name in ("up_raw", "dn_raw", "up", "dn"):
+        agree = np.mean(L[name] == getattr(ref, name))
+        print(name, "agreement", agree)
+        assert agree >= CONCORDANCE_MIN, (name, agree)
+
+
+def test_a4_start_hits(both1):
+    ev, out, dbg, ref = both1
+    g = set(tracklets_by_start(dbg))
+    o = set(ref.starts.tolist())
+    sym = len(g ^ o)
+    print("starts gpu %d oracle %d differ %d" % (len(g), len(o), sym))
+    assert sym <= (1 - CONCORDANCE_MIN) * len(o)
+
+
+def test_a5_tracklets(both1):
+    ev, out, dbg, ref = both1
+    g = tracklets_by_start(dbg)
+    nsame = ndiff = 0
+    worst = np.zeros(5)
+    for t, s in enumerate(ref.starts.tolist()):
+        if s not in g:
+            ndiff += 1
+            continue
+        gt = g[s]
+        oh = ref.tracklet_hits(t)
+        if gt["n"] != ref.tl_nhits[t] or not np.array_equal(gt["hits"], oh):
+            ndiff += 1
+            continue
+        nsame += 1
+        if gt["n"] >= 3:
+            rel = np.abs(gt["par"] - ref.tl_par[t]) / np.maximum(np.abs(ref.tl_par[t]), concordance.SCALES)
+            worst = np.maximum(worst, rel)
+    print("tracklets identical %d differ %d worst par rel %s" % (nsame, ndiff, worst))
+    assert ndiff <= (1 - CONCORDANCE_MIN) * (nsame + ndiff) + 1
+    assert worst.max() <= PAR_REL
+
+
+def test_a6_ownership(both1):
+    ev, out, dbg, ref = both1
+    own_g = owners_by_start(dbg, ev.n)
+    own_o = np.where(ref.owner >= 0, ref.starts[np.maximum(ref.owner, 0)], -1)
+    agree = np.mean(own_g == own_o)
+    print("owner agreement", agree)
+    assert agree >= CONCORDANCE_MIN
+
+
+def test_a7_tracks(both1):
+    ev, out, dbg, ref = both1
+    c = compare_tracks(ev, out, ref)
+    print("tracks gpu %d oracle %d matched %d exact %d concordance %.7f" % (
+        c["n_test"], c["n_ref"], c["n_matched"], c["n_exact"], c["concordance"]))
+    assert c["concordance"] >= CONCORDANCE_MIN
+    assert c["n_exact"] >= c["n_matched"] - max(1, int((1 - CONCORDANCE_MIN) * c["n_matched"]))
+    assert c["par_rel_max"].max() <= PAR_REL, c["par_rel_max"]
+    # canonical order (Section 3.2): innermost cluster's input index increases
+    inner = out["hits"][out["first"]]
+    assert np.all(np.diff(inner) > 0)
+    # every output cluster on its own row, inner to outer, owned once
+    for m in range(len(out["first"])):
+        h = out["hits"][out["first"][m]:out["first"][m] + out["nhits"][m]]
+        assert np.all(np.diff(ev.row[h].astype(int)) > 0)
+    assert np.unique(out["hits"]).size == out["hits"].size
+    assert np.all(out["nhits"] >= 30)
+
+
+def test_error_against_fp64_oracle(both1):
+    """States the per-parameter error of the float GPU path against the double oracle."""
+    ev, out, dbg, ref = both1
+    ref64 = run_oracle(ev, precision=64, key="c1")
+    c = compare_tracks(ev, out, ref64)
+    print("vs FP64: concordance %.7f mean rel %s max rel %s" % (c["concordance"], c["par_rel_mean"], c["par_rel_max"]))
+    assert c["concordance"] >= 0.999
+    assert np.all(c["par_rel_mean"] < 1e-3)
+
+
+# ---------------------------------------------------------------------------------------------
+# full size and edge cases
+# ---------------------------------------------------------------------------------------------
+def test_full_central_event():
+    """The benchmark workload (central-like event, 3.3 M clusters) end to end."""
+    ev = eventgen.config_event(2)
+    tr, out, dbg = run_gpu(ev, debug=False)
+    ref = run_oracle(ev, key="c2")
+    c = compare_tracks(ev, out, ref)
+    print("central: gpu %d oracle %d concordance %.7f exact %d/%d par max %s" % (
+        c["n_test"], c["n_ref"], c["concordance"], c["n_exact"], c["n_matched"], c["par_rel_max"]))
+    assert c["concordance"] >= CONCORDANCE_MIN
+    assert c["par_rel_max"].max() <= PAR_REL
+    tr.close()
+
+
+def test_single_sector_config0(ev0):
+    tr, out, dbg = run_gpu(ev0)
+    ref = run_oracle(ev0, key="c0")
+    c = compare_tracks(ev0, out, ref)
+    assert c["concordance"] >= CONCORDANCE_MIN and c["n_exact"] == c["n_matched"] == c["n_ref"]
+    tr.close()
+
+
+def test_empty_event():
+    geo = eventgen.Geometry()
+    tr = Tracker.for_geometry(geo)
+    e = torch.zeros(0, device="cuda")
+    res = tr.track(e, e, torch.zeros(0, dtype=torch.uint8, device="cuda"), np.zeros(36 * 159, np.int32))
+    assert res.sync() == (0, 0)
+    res.release()
+    tr.close()
+
+
+def test_sparse_and_ragged_rows():
+    """Rows with 0, 1 and 2 clusters, and a single track crossing empty rows."""
+    geo = eventgen.Geometry()
+    spec = eventgen.EventSpec(n_primaries=3, efficiency=0.7, noise_frac=0.0, pt_cut=0.3)
+    ev = eventgen.generate_event(spec, geo, seed=9)
+    tr, out, dbg = run_gpu(ev)
+    ref = run_oracle(ev)
+    c = compare_tracks(ev, out, ref)
+    assert c["concordance"] == 1.0
+    tr.close()
+
+
+def test_noisy_sector():
+    """One sector filled with noise (Section 6: noise-filled sectors after trip recovery)."""
+    geo = eventgen.Geometry()
+    spec = eventgen.EventSpec(n_primaries=300, noise_frac=0.1)
+    ev = eventgen.generate_event(spec, geo, seed=13)
+    rng = np.random.default_rng(0)
+    extra_n = 159 * 4500            # 4500 noise clusters on every row of sector 4: beyond shared-memory staging
+    rows = np.repeat(np.arange(159), 4500)
+    half = geo.row_x[rows] * geo.tan_half
+    ys = (rng.uniform(-1, 1, extra_n) * half).astype(np.float32)
+    zs = rng.uniform(0, 250, extra_n).astype(np.float32)
+    sec = ev.sector_of()
+    y = np.concatenate([ev.y, ys])
+    z = np.concatenate([ev.z, zs])
+    row = np.concatenate([ev.row, rows.astype(np.uint8)])
+    s = np.concatenate([sec, np.full(extra_n, 4)])
+    order = np.lexsort((row, s))
+    counts = np.bincount(s.astype(np.int64) * 159 + row, minlength=36 * 159).astype(np.int32)
+    ev2 = eventgen.Event(geo, spec, 13, 0, y[order], z[order], row[order], counts,
+                         np.concatenate([ev.label, np.full(extra_n, -1)])[order], ev.particles)
+    tr, out, dbg = run_gpu(ev2, debug=False)
+    ref = run_oracle(ev2)
+    c = compare_tracks(ev2, out, ref)
+    print("noisy sector: concordance %.7f tracks %d/%d" % (c["concordance"], c["n_test"], c["n_ref"]))
+    assert c["concordance"] >= CONCORDANCE_MIN
+    tr.close()
+
+
+@pytest.mark.parametrize("tuning", [
+    dict(bin_occupancy=0.5), dict(bin_occupancy=16.0), dict(stage_rows=0),
+    dict(neighbours_block=64, construct_block=64), dict(construct_block=256, construct_ctas_per_sm=1)])
+def test_tuning_does_not_change_results(tuning):
+    """Grid bin size, block shapes and staging only change speed (the autotuner relies on it)."""
+    ev = _small36()
+    tr, base, _ = run_gpu(ev, debug=False)
+    tr.set_tuning(tuning)
+    _, out, _ = run_gpu(ev, tracker=tr, debug=False)
+    for k in base:
+        assert np.array_equal(base[k], out[k]), (tuning, k)
+    tr.close()
+
+
+def test_batch_equals_one_at_a_time():
+    evs = [eventgen.config_event(3, event=i) for i in range(3)]
+    geo = evs[0].geometry
+    tr = Tracker.for_geometry(geo)
+    singles = []
+    for ev in evs:
+        _, out, _ = run_gpu(ev, tracker=tr, debug=False)
+        singles.append(out)
+    y = torch.from_numpy(np.concatenate([e.y for e in evs])).cuda()
+    z = torch.from_numpy(np.concatenate([e.z for e in evs])).cuda()
+    row = torch.from_numpy(np.concatenate([e.row for e in evs])).cuda()
+    counts = np.concatenate([e.counts for e in evs])
+    res = tr.track_batch(y, z, row, counts, len(evs))
+    res.sync()
+    b = res.to_numpy()
+    res.release()
+    off = 0
+    for i, (ev, s) in enumerate(zip(evs, singles)):
+        sel = b["event"] == i
+        assert sel.sum() == len(s["first"])
+        for k in ("par", "cov", "x_ref", "chi2", "ndf", "nhits", "sector"):
+            assert np.array_equal(b[k][sel], s[k]), k
+        hb = np.concatenate([b["hits"][f:f + n] for f, n in zip(b["first"][sel], b["nhits"][sel])])
+        assert np.array_equal(hb - off, s["hits"])
+        off += ev.n
+    tr.close()
+
+
+def test_host_input_path_equals_device_path(ev1):
+    tr, dev_out, _ = run_gpu(ev1, debug=False)
+    res = tr.track_host(ev1.y, ev1.z, ev1.row, ev1.counts)
+    res.sync()
+    host_out = res.to_numpy()
+    res.release()
+    for k in dev_out:
+        assert np.array_equal(dev_out[k], host_out[k]), k
+    tr.close()
+
+
+def test_repeated_calls_are_deterministic(ev1):
+    tr, a, _ = run_gpu(ev1, debug=False)
+    _, b, _ = run_gpu(ev1, tracker=tr, debug=False)
+    for k in a:
+        assert np.array_equal(a[k], b[k]), k
+    tr.close()
+
+
+# ---------------------------------------------------------------------------------------------
+# errors come back as status codes
+# ---------------------------------------------------------------------------------------------
+def test_wrong_row_byte_is_reported(ev0):
+    tr = Tracker.for_geometry(ev0.geometry)
+    y, z, row = to_device(ev0)
+    row[100] = (int(row[100].item()) + 1) % 159
+    res = tr.track(y, z, row, ev0.counts)
+    with pytest.raises(TrackerError) as e:
+        res.sync()
+    assert e.value.status == 1 and "ingest" in str(e.value)
+    res.release()
+    tr.close()
+
+
+def test_bad_counts_rejected_on_host(ev0):
+    tr = Tracker.for_geometry(ev0.geometry)
+    y, z, row = to_device(ev0)
+    bad = ev0.counts.copy()
+    bad[3] += 1
+    with pytest.raises(TrackerError) as e:
+        tr.track(y, z, row, bad)
+    assert e.value.status == 1
+    tr.close()
+
+
+def test_budget_is_enforced(ev1):
+    geo = ev1.geometry
+    tr = Tracker.for_geometry(geo, budget=1 << 20)
+    y, z, row = to_device(ev1)
+    with pytest.raises(TrackerError) as e:
+        tr.track(y, z, row, ev1.counts)
+    assert e.value.status == 3
+    tr.close()
