@@ -236,6 +236,41 @@ int tpc_tracker_set_timing(tpc_tracker *tr, int enable);
  * Errors: TPC_ERR_INVALID_ARG, TPC_ERR_CUDA. */
 int tpc_result_stats(tpc_result *res, tpc_call_stats *st);
 
+/* Largest event tpc_find_links_noalloc accepts: clusters, and row units
+ * (n_sectors * n_rows of one event). */
+#define TPC_NOALLOC_MAX_CLUSTERS 1048576
+#define TPC_NOALLOC_MAX_UNITS (36 * 255)
+
+/* Neighbours finder and evolution (the cellular-automaton links) of one event,
+ * without allocating any device memory.  The paper has no counterpart: this
+ * entry point exists for callers that cannot call cudaMalloc, for instance code
+ * that runs inside a framework which hands all device memory to its own
+ * allocator at start-up, or a real-time process that must not allocate (nor
+ * synchronise the device the way cudaMalloc can) once data taking has started.
+ *
+ * Inputs as for tpc_track_event: y, z, row device arrays of n clusters, counts a
+ * HOST array of n_sectors * n_rows counts.  Outputs (device, caller-owned):
+ * up[i], dn[i] = input index of the cluster linked to cluster i on the next /
+ * previous row after the evolution step, -1 for none.  status (device, may be
+ * NULL) receives 4 ints: device-side status, event, sector, stage (as
+ * tpc_last_error_detail).  All work is ordered on `stream`.
+ *
+ * The intermediate data (binned clusters, grids, raw links) live in one static
+ * device array of about 31 MB sized for TPC_NOALLOC_MAX_CLUSTERS clusters; it is
+ * reserved on each GPU whose copy of this part of the library has been loaded
+ * and stays there until the process exits.  Every call uses the same array and
+ * it keeps the previous call's contents, so calls whose GPU work overlaps (two
+ * streams, two threads, two trackers) race and corrupt each other: order them on
+ * one stream or synchronise between them.  The first call on a device looks up
+ * the array's device address (cudaGetSymbolAddress); make that first call before
+ * any stream capture.
+ * Errors (returned): TPC_ERR_INVALID_ARG (NULL pointers with n > 0, counts not
+ * summing to n, n > TPC_NOALLOC_MAX_CLUSTERS, more row units than
+ * TPC_NOALLOC_MAX_UNITS), TPC_ERR_CUDA. */
+int tpc_find_links_noalloc(tpc_tracker *tr, const float *y, const float *z, const uint8_t *row,
+                           const int32_t *counts, int64_t n, int32_t *up, int32_t *dn,
+                           int32_t *status, void *stream);
+
 /* Intermediate buffers of the tracker's last call, for per-stage checks.  Device
  * pointers into the tracker's workspace; valid until its next call.  Cluster
  * slots are "sorted" positions: slot j of row unit u = (event * n_sectors +

@@ -90,6 +90,22 @@ struct tpc_result {
     cudaEvent_t stage_ev[8] = {};
 };
 
+bool tpc::tracker_info(const tpc_tracker *tr, TrackerInfo *out)
+{
+    if (!tr || !out) return false;
+    out->dc = &tr->dc;
+    out->row_x = tr->row_x;
+    out->n_rows = tr->n_rows;
+    out->n_sectors = tr->n_sectors;
+    out->num_sms = tr->num_sms;
+    out->tan_half = tr->tan_half;
+    out->z_max = tr->z_max;
+    out->bin_occupancy = tr->tuning.bin_occupancy;
+    out->neighbours_block = tr->tuning.neighbours_block;
+    out->stage_rows = tr->tuning.stage_rows;
+    return true;
+}
+
 static int cuda_fail(cudaError_t e)
 {
     if (e != cudaSuccess) {

@@ -3,6 +3,8 @@
 #include <cstdint>
 #include <cuda_runtime.h>
 
+struct tpc_tracker;
+
 namespace tpc {
 
 constexpr int kMaxRows = 255;       // row index is a uint8
@@ -163,4 +165,15 @@ int launch_select(const DevConst &c, const Workspace &w, int64_t n_input, const 
 int launch_output(const DevConst &c, const Workspace &w, const OutBuffers &o, int64_t n_input,
                    const LaunchCfg &lc, cudaStream_t s);
 int neighbours_smem_limit();
+
+// Read-only view of a tracker's constants for entry points defined outside api.cu.
+struct TrackerInfo {
+    const DevConst *dc;
+    const float *row_x;
+    int n_rows, n_sectors, num_sms;
+    float tan_half, z_max;
+    float bin_occupancy;
+    int neighbours_block, stage_rows;
+};
+bool tracker_info(const struct ::tpc_tracker *tr, TrackerInfo *out);
 }  // namespace tpc

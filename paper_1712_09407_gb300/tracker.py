@@ -85,6 +85,8 @@ EXPORTS = {
     "tpc_tracker_debug_view": (c_int, [c_void_p, P(tpc_debug_view)]),
     "tpc_tracker_set_timing": (c_int, [c_void_p, c_int]),
     "tpc_result_stats": (c_int, [c_void_p, P(tpc_call_stats)]),
+    "tpc_find_links_noalloc": (c_int, [c_void_p, c_void_p, c_void_p, c_void_p, c_void_p, c_int64, c_void_p,
+                                       c_void_p, c_void_p, c_void_p]),
 }
 
 
@@ -241,6 +243,16 @@ def tpc_result_stats(res) -> dict:
     return dict(ms=list(st.ms)[:7], kernel_launches=st.kernel_launches, clusters=st.clusters,
                 tracklets=st.tracklets, row_visits=st.row_visits, candidates=st.candidates, tracks=st.tracks,
                 hits=st.hits)
+
+
+def tpc_find_links_noalloc(tr, y, z, row, counts, up, dn, status=None, stream=None, n=None):
+    """Links after the evolution step for one event, with no device allocation by the library.
+    ``up``/``dn`` (int32 device tensors of n) receive input indices (-1 = none); ``status``
+    (optional int32 device tensor of 4) receives the device-side status.  Returns the C status."""
+    counts = np.ascontiguousarray(counts, dtype=np.int32)
+    n = int(y.shape[0]) if n is None else int(n)
+    return lib().tpc_find_links_noalloc(tr, _ptr(y), _ptr(z), _ptr(row), counts.ctypes.data, n, _ptr(up), _ptr(dn),
+                                        _ptr(status), _stream(stream))
 
 
 def tpc_tracker_debug_view(tr) -> tpc_debug_view:
