@@ -43,11 +43,35 @@ def parse():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--workload", default="central", choices=["central", "batch"],
+                    help="central: the metric's workload (default); batch: 64 events per call vs one at a time")
+    ap.add_argument("--batch-events", type=int, default=64)
     return ap.parse_args()
 
 
 def dist_env():
     return int(os.environ.get("RANK", 0)), int(os.environ.get("WORLD_SIZE", 1)), int(os.environ.get("LOCAL_RANK", 0))
+
+
+def reduce_max(x: float, world: int, device: str = "cpu") -> float:
+    """Maximum of x over all ranks (the slowest replica sets the job time)."""
+    if world <= 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def replica_throughput(max_total_s: float, steps: int, world: int) -> float:
+    """Whole-job events/s: every rank tracks `steps` events of its own (weak scaling)."""
+    return world * steps / max_total_s
+
+
+def replica_event(rank: int) -> int:
+    """Event index of the central-like workload a rank tracks (replicas do not share events)."""
+    return rank
 
 
 # ------------------------------------------------------------------------------------------------
@@ -198,7 +222,7 @@ def run_ours(args):
     from paper_1712_09407_gb300 import eventgen
     from paper_1712_09407_gb300.tracker import Tracker
 
-    ev = eventgen.config_event(2, event=rank)           # one replica per GPU, its own event
+    ev = eventgen.config_event(2, event=replica_event(rank))   # one replica per GPU, its own event
     tr = Tracker.for_geometry(ev.geometry)
     tr.reserve(ev.n, 1)
     stream = torch.cuda.Stream()
@@ -248,12 +272,8 @@ def run_ours(args):
         r.release()
     del results
     step_ms = [s.elapsed_time(e) for s, e in zip(starts, ends)]
-    total_s = sum(step_ms) / 1e3
-    if world > 1:
-        t = torch.tensor([total_s], device="cuda")
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        total_s = float(t.item())
-    value = world * args.steps / total_s
+    total_s = reduce_max(sum(step_ms) / 1e3, world, "cuda")
+    value = replica_throughput(total_s, args.steps, world)
     tr.set_timing(False)
 
     # ---- end to end through the host-buffer entry point
@@ -287,11 +307,7 @@ def run_ours(args):
                     times.append(t1 - t0)
                 h2d = ev.n * 9
                 d2h = M * (5 + 15 + 3 + 5) * 4 + H * 4 + 48
-        e2e_v = len(times) / sum(times)
-        if world > 1:
-            t = torch.tensor([sum(times)], device="cuda")
-            torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-            e2e_v = world * len(times) / float(t.item())
+        e2e_v = replica_throughput(reduce_max(sum(times), world, "cuda"), len(times), world)
         e2e = {"value": e2e_v, "unit": "events/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
                "path": "tpc_track_event_host (pinned host input) + tpc_result_copy_to_host, wall clock"}
 
@@ -327,10 +343,76 @@ def run_ours(args):
     return 0
 
 
+def run_batch(args):
+    """64 events of the batched workload (primaries log-uniform in [500, 16000], noise 5-20 %)
+    tracked by one call (every stage launched once over all sectors of all events) against the
+    same events tracked one call each; both from HBM-resident inputs, L2 flushed before each
+    timed call."""
+    import torch
+    from __graft_entry__ import build
+    build()
+    from paper_1712_09407_gb300 import eventgen
+    from paper_1712_09407_gb300.serving import event_pool
+    from paper_1712_09407_gb300.tracker import Tracker
+
+    pool = event_pool(args.batch_events)
+    n_tot = sum(p[4] for p in pool)
+    y = torch.cat([p[0] for p in pool]).cuda()
+    z = torch.cat([p[1] for p in pool]).cuda()
+    row = torch.cat([p[2] for p in pool]).cuda()
+    counts = np.concatenate([p[3] for p in pool])
+    offs = np.concatenate([[0], np.cumsum([p[4] for p in pool])])
+    tr = Tracker.for_geometry(eventgen.Geometry())
+    tr.reserve(n_tot, len(pool))
+    stream = torch.cuda.Stream()
+    flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+
+    def timed(fn, reps):
+        ms = []
+        with torch.cuda.stream(stream):
+            for k in range(args.warmup + reps):
+                flush.fill_(float(k))
+                a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                a.record(stream)
+                rs = fn()
+                b.record(stream)
+                for r in rs:
+                    r.sync()
+                    r.release()
+                if k >= args.warmup:
+                    ms.append(a.elapsed_time(b))
+        return float(np.median(ms))
+
+    def batched():
+        return [tr.track_batch(y, z, row, counts, len(pool), stream=stream)]
+
+    def singles():
+        out = []
+        for i in range(len(pool)):
+            out.append(tr.track(y[offs[i]:offs[i + 1]], z[offs[i]:offs[i + 1]], row[offs[i]:offs[i + 1]],
+                                pool[i][3], stream=stream))
+        return out
+
+    reps = max(3, min(args.steps, 10))
+    t_b = timed(batched, reps)
+    t_s = timed(singles, reps)
+    line = {"metric": "batched events/s", "value": len(pool) / (t_b / 1e3), "unit": "events/s", "n_gpus": 1,
+            "steps": reps, "warmup": args.warmup, "ms_per_step": t_b, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": "%d events, primaries log-uniform 500-16000, noise 5-20 %%, 36 sectors, seeds (1, i)"
+                                   % len(pool), "clusters": int(n_tot), "l2": "flushed before every step"},
+            "one_at_a_time": {"value": len(pool) / (t_s / 1e3), "ms_per_step": t_s},
+            "speedup_vs_one_at_a_time": t_s / t_b}
+    print(json.dumps(line))
+    return 0
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         return run_reference(args)
+    if args.workload == "batch":
+        return run_batch(args)
     return run_ours(args)
 
 

@@ -98,7 +98,7 @@ typedef struct {
 typedef struct {
     float bin_occupancy;       /* target clusters per grid cell (>0) */
     int neighbours_block;      /* threads per CTA of the neighbours finder (multiple of 32, <= 256) */
-    int construct_block;       /* threads per CTA of the tracklet constructor (multiple of 32, <= 256) */
+    int construct_block;       /* threads per CTA of the tracklet constructor (multiple of 32, <= 128) */
     int construct_ctas_per_sm; /* persistent CTAs per SM of the constructor (0 = occupancy limit) */
     int stage_rows;            /* 1: stage rows k-1, k+1 into shared memory with bulk copies */
 } tpc_tuning;
@@ -187,6 +187,11 @@ int tpc_track_event_host(tpc_tracker *tr, const float *y, const float *z, const 
  * TPC_ERR_INVALID_ARG (a cluster's row byte disagrees with counts),
  * TPC_ERR_CAPACITY, TPC_ERR_TIMEOUT, or TPC_ERR_CUDA. */
 int tpc_result_sync_counts(tpc_result *res, int64_t *n_tracks, int64_t *n_hits);
+
+/* Non-blocking completion test: 1 if the result's work has finished (a following
+ * tpc_result_sync_counts returns at once), 0 if it is still running, or a negative
+ * TPC_ERR_* value (-TPC_ERR_CUDA) if the query failed. */
+int tpc_result_ready(tpc_result *res);
 
 /* Fill *view with device pointers to the result.  Requires a successful
  * tpc_result_sync_counts first (TPC_ERR_STATE otherwise). */

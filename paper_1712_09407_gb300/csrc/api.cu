@@ -66,6 +66,7 @@ struct tpc_tracker {
     int next_staging = 0;
     std::vector<int4> meta;
     std::vector<int2> dims;
+    std::vector<tpc_result *> free_results;   // released results, reused without new pinned allocations
     // last call
     int64_t last_units = 0, last_slots = 0, last_n = 0;
     bool timing = false;
@@ -149,10 +150,11 @@ extern "C" void tpc_params_default(tpc_params *p)
 extern "C" void tpc_tuning_default(tpc_tuning *t)
 {
     if (!t) return;
-    t->bin_occupancy = 2.0f;
-    t->neighbours_block = 128;
+    // picked by the autotuner on the central-like event on a GB300
+    t->bin_occupancy = 0.5f;
+    t->neighbours_block = 256;
     t->construct_block = 128;
-    t->construct_ctas_per_sm = 0;
+    t->construct_ctas_per_sm = 10;
     t->stage_rows = 1;
 }
 
@@ -249,7 +251,7 @@ extern "C" int tpc_tracker_set_tuning(tpc_tracker *tr, const tpc_tuning *t)
 {
     if (!tr || !t) return TPC_ERR_INVALID_ARG;
     if (!(t->bin_occupancy >= 0.5f) || t->neighbours_block < 32 || t->neighbours_block > 256 ||
-        t->neighbours_block % 32 || t->construct_block < 32 || t->construct_block > 256 ||
+        t->neighbours_block % 32 || t->construct_block < 32 || t->construct_block > 128 ||
         t->construct_block % 32 || t->construct_ctas_per_sm < 0)
         return TPC_ERR_INVALID_ARG;
     tr->tuning = *t;
@@ -278,6 +280,7 @@ static size_t carve(tpc_tracker *tr, const WsSizes &s, Alloc &a)
     w.meta = a.take<int4>(s.R);
     w.dims = a.take<int2>(s.R);
     w.grid = a.take<float4>(s.R);
+    w.rgi = a.take<int4>(s.R);
     w.cell = a.take<int32_t>(s.C);
     w.yz = a.take<float2>(s.P);
     w.orig = a.take<int32_t>(s.P);
@@ -287,6 +290,8 @@ static size_t carve(tpc_tracker *tr, const WsSizes &s, Alloc &a)
     w.dn = a.take<int32_t>(s.P);
     w.ckey = a.take<unsigned long long>(s.P);
     w.starts = a.take<int4>(s.T);
+    w.order = a.take<int32_t>(s.T);
+    w.buckets = a.take<int32_t>(2 * kOrderBuckets);
     w.tl_n = a.take<int32_t>(s.T);
     w.tl_hits = a.take<int32_t>(s.T * tr->n_rows);
     w.tl_par = a.take<float>(5 * s.T);
@@ -312,6 +317,8 @@ static size_t carve(tpc_tracker *tr, const WsSizes &s, Alloc &a)
     w.wcap = s.W;
     return a.used;
 }
+
+static void destroy_result(tpc_result *r);
 
 static int reserve(tpc_tracker *tr, int64_t n, int64_t events)
 {
@@ -394,24 +401,40 @@ static int run(tpc_tracker *tr, const float *y, const float *z, const uint8_t *r
     if (n_total > 0 && (!y || !z || !row)) return TPC_ERR_INVALID_ARG;
     int s = reserve(tr, n_total, n_events);
     if (s != TPC_OK) return s;
-    // result memory
-    tpc_result *res = new (std::nothrow) tpc_result();
-    if (!res) return TPC_ERR_CUDA;
+    // result object: reuse a released one (its pinned count buffer and events) when possible
+    tpc_result *res = nullptr;
+    if (!tr->free_results.empty()) {
+        res = tr->free_results.back();
+        tr->free_results.pop_back();
+        cudaEvent_t keep_done = res->done;
+        int32_t *keep_counts = res->h_counts;
+        cudaEvent_t keep_ev[8];
+        memcpy(keep_ev, res->stage_ev, sizeof keep_ev);
+        *res = tpc_result();
+        res->done = keep_done;
+        res->h_counts = keep_counts;
+        memcpy(res->stage_ev, keep_ev, sizeof keep_ev);
+    } else {
+        res = new (std::nothrow) tpc_result();
+        if (!res) return TPC_ERR_CUDA;
+    }
     res->tr = tr;
     res->stream = st;
-    const int64_t tcap = tr->w.tcap;
+    // tracks <= tracklets <= n / min_chain (chains of one-to-one links are disjoint)
+    const int64_t tbound = n_total / (tr->params.min_chain > 0 ? tr->params.min_chain : 1) + 64;
+    const int64_t tcap = tr->w.tcap < tbound ? tr->w.tcap : tbound;
     const int64_t hcap = n_total;
     res->bytes = result_bytes(tcap, hcap);
     if (tr->budget && tr->bytes_ws + tr->bytes_results + res->bytes > tr->budget) {
-        delete res;
+        tr->free_results.push_back(res);
         return TPC_ERR_BUDGET;
     }
     if (cudaMallocAsync(&res->dev, res->bytes, st) != cudaSuccess ||
-        cudaMallocHost((void **)&res->h_counts, kCountWords * sizeof(int32_t)) != cudaSuccess ||
-        cudaEventCreateWithFlags(&res->done, cudaEventDisableTiming) != cudaSuccess) {
+        (!res->h_counts && cudaMallocHost((void **)&res->h_counts, kCountWords * sizeof(int32_t)) != cudaSuccess) ||
+        (!res->done && cudaEventCreateWithFlags(&res->done, cudaEventDisableTiming) != cudaSuccess)) {
         if (res->dev) cudaFreeAsync(res->dev, st);
-        if (res->h_counts) cudaFreeHost(res->h_counts);
-        delete res;
+        res->dev = nullptr;
+        destroy_result(res);
         return TPC_ERR_CUDA;
     }
     tr->bytes_results += res->bytes;
@@ -458,9 +481,8 @@ static int run(tpc_tracker *tr, const float *y, const float *z, const uint8_t *r
         // cannot happen with ws_sizes' bounds; guard anyway
         tr->bytes_results -= res->bytes;
         cudaFreeAsync(res->dev, st);
-        cudaFreeHost(res->h_counts);
-        cudaEventDestroy(res->done);
-        delete res;
+        res->dev = nullptr;
+        destroy_result(res);
         return TPC_ERR_CAPACITY;
     }
     int smem = smem_need < neighbours_smem_limit() ? smem_need : neighbours_smem_limit();
@@ -487,7 +509,8 @@ static int run(tpc_tracker *tr, const float *y, const float *z, const uint8_t *r
     if (tr->ws_used) TPC_CUDA(cudaStreamWaitEvent(st, tr->ws_done, 0));
     const bool timed = tr->timing;
     if (timed) {
-        for (auto &e : res->stage_ev) TPC_CUDA(cudaEventCreate(&e));
+        for (auto &e : res->stage_ev)
+            if (!e) TPC_CUDA(cudaEventCreate(&e));
         TPC_CUDA(cudaEventRecord(res->stage_ev[0], st));
     }
     res->timed = timed;
@@ -610,6 +633,16 @@ extern "C" int tpc_result_sync_counts(tpc_result *r, int64_t *n_tracks, int64_t 
     return r->status;
 }
 
+extern "C" int tpc_result_ready(tpc_result *r)
+{
+    if (!r) return -TPC_ERR_INVALID_ARG;
+    if (r->synced) return 1;
+    cudaError_t e = cudaEventQuery(r->done);
+    if (e == cudaSuccess) return 1;
+    if (e == cudaErrorNotReady) return 0;
+    return -TPC_ERR_CUDA;
+}
+
 extern "C" int tpc_result_get(tpc_result *r, tpc_track_view *v)
 {
     if (!r || !v) return TPC_ERR_INVALID_ARG;
@@ -659,17 +692,20 @@ extern "C" void tpc_result_release(tpc_result *r)
 {
     if (!r) return;
     if (r->dev) cudaFreeAsync(r->dev, r->stream);
-    if (r->done) {
-        cudaEventSynchronize(r->done);
-        cudaEventDestroy(r->done);
-    }
+    r->dev = nullptr;
+    if (r->done) cudaEventSynchronize(r->done);
+    std::lock_guard<std::mutex> g(r->tr->mu);
+    r->tr->bytes_results -= r->bytes;
+    r->bytes = 0;
+    r->tr->free_results.push_back(r);      // pinned counts and events are kept for the next call
+}
+
+static void destroy_result(tpc_result *r)
+{
+    if (r->done) cudaEventDestroy(r->done);
     if (r->h_counts) cudaFreeHost(r->h_counts);
     for (auto &e : r->stage_ev)
         if (e) cudaEventDestroy(e);
-    {
-        std::lock_guard<std::mutex> g(r->tr->mu);
-        r->tr->bytes_results -= r->bytes;
-    }
     delete r;
 }
 
@@ -685,6 +721,7 @@ extern "C" void tpc_tracker_destroy(tpc_tracker *tr)
         if (s.consumed) cudaEventDestroy(s.consumed);
     }
     if (tr->ws_done) cudaEventDestroy(tr->ws_done);
+    for (tpc_result *r : tr->free_results) destroy_result(r);
     delete tr;
 }
 

@@ -13,6 +13,7 @@ constexpr int kCellMax = 1024;      // grid cells per row unit (host clamps)
 constexpr int kSlotAlign = 8;       // sorted row segments start on 8-element (32 B) boundaries
 constexpr int kCellAlign = 4;       // cell-start segments start on 16 B boundaries
 constexpr unsigned kFull = 0xffffffffu;
+constexpr int kOrderBuckets = 512;  // >= 2 * kMaxRows + 2 (expected-work keys)
 
 // Error word layout in the workspace: [0] status, [1] event, [2] sector, [3] stage.
 enum { ERR_STATUS = 0, ERR_EVENT = 1, ERR_SECTOR = 2, ERR_STAGE = 3 };
@@ -59,6 +60,7 @@ struct Workspace {
     int4 *meta;            // {in_off, n, s_off, cell_off}
     int2 *dims;            // {ny, nz}
     float4 *grid;          // {ymin, zmin, 1/dy, 1/dz}
+    int4 *rgi;             // {s_off, cell_off, ny, nz}: what a row search needs, in one 16 B load
     int32_t *cell;         // cell starts relative to the row's first slot
     // per cluster slot (sorted order, padded per row unit)
     float2 *yz;
@@ -67,6 +69,8 @@ struct Workspace {
     unsigned long long *ckey;   // A6 claims
     // per tracklet
     int4 *starts;          // {first, mid, last, (sector << 16) | (chain length << 8) | row}
+    int32_t *order;        // tracklets in the order the constructor takes them (longest expected first)
+    int32_t *buckets;      // [kOrderBuckets * 2] histogram / cursors of the ordering sort
     int32_t *tl_n;
     int32_t *tl_hits;      // [tcap * nr]
     float *tl_par;         // [5 * tcap]

@@ -217,27 +217,24 @@ __device__ __forceinline__ bool seed3(const float x[3], const float y[3], const 
 }
 
 // Best cluster of one row unit for a predicted state: minimum chi2 inside the window,
-// ties to the lower input index.  Returns the slot or -1.
-__device__ __forceinline__ int search_row(const DevConst &c, const Workspace &w, int unit, const KF &pr,
-                                          const Gain &g, float &chi2_out, int &ncand)
+// ties to the lower input index.  rg = {slot offset, cell offset, ny, nz}, gr = {ymin, zmin,
+// 1/dy, 1/dz} of the unit.  Returns the slot or -1.
+__device__ __forceinline__ int search_row(const DevConst &c, const Workspace &w, const int4 rg, const float4 gr,
+                                          const KF &pr, const Gain &g, float &chi2_out, int &ncand)
 {
-    const int4 m = __ldg(&w.meta[unit]);
-    if (m.y == 0) return -1;
-    const int2 d = __ldg(&w.dims[unit]);
-    const float4 gr = __ldg(&w.grid[unit]);
     const float wy = c.nsig * sqrtf(pr.c00 + c.sy2);
     const float wz = c.nsig * sqrtf(pr.c11 + c.sz2);
     const float y = pr.p0, z = pr.p1;
-    const int iy0 = cell1(y - wy - kBinSlack, gr.x, gr.z, d.x);
-    const int iy1 = cell1(y + wy + kBinSlack, gr.x, gr.z, d.x);
-    const int iz0 = cell1(z - wz - kBinSlack, gr.y, gr.w, d.y);
-    const int iz1 = cell1(z + wz + kBinSlack, gr.y, gr.w, d.y);
-    const int32_t *cell = w.cell + m.w;
-    const float2 *yz = w.yz + m.z;
+    const int iy0 = cell1(y - wy - kBinSlack, gr.x, gr.z, rg.z);
+    const int iy1 = cell1(y + wy + kBinSlack, gr.x, gr.z, rg.z);
+    const int iz0 = cell1(z - wz - kBinSlack, gr.y, gr.w, rg.w);
+    const int iz1 = cell1(z + wz + kBinSlack, gr.y, gr.w, rg.w);
+    const int32_t *cell = w.cell + rg.y;
+    const float2 *yz = w.yz + rg.x;
     int best = -1, borig = -1;       // borig: input index of the best slot, loaded on the first tie
     float bc = 0.0f;
     for (int iz = iz0; iz <= iz1; iz++) {
-        const int a = __ldg(cell + iz * d.x + iy0), e = __ldg(cell + iz * d.x + iy1 + 1);
+        const int a = __ldg(cell + iz * rg.z + iy0), e = __ldg(cell + iz * rg.z + iy1 + 1);
         ncand += e - a;
         for (int j = a; j < e; j++) {
             const float2 q = __ldg(yz + j);
@@ -248,8 +245,8 @@ __device__ __forceinline__ int search_row(const DevConst &c, const Workspace &w,
                 bc = x2;
                 borig = -1;
             } else if (x2 == bc) {
-                if (borig < 0) borig = __ldg(w.orig + m.z + best);
-                const int o = __ldg(w.orig + m.z + j);
+                if (borig < 0) borig = __ldg(w.orig + rg.x + best);
+                const int o = __ldg(w.orig + rg.x + j);
                 if (o < borig) {
                     best = j;
                     borig = o;
@@ -258,10 +255,67 @@ __device__ __forceinline__ int search_row(const DevConst &c, const Workspace &w,
         }
     }
     chi2_out = bc;
-    return best < 0 ? -1 : m.z + best;
+    return best < 0 ? -1 : rg.x + best;
 }
 
-__global__ void __launch_bounds__(256)
+// ---------------------------------------------------------------------------------------------
+// Longest-expected-first order of the tracklets (counting sort on a small key), so that the
+// work queue hands out the long tracklets first and ends on short ones.  A chain of 4 or more
+// clusters usually belongs to a real track, which runs outwards from its start row to the last
+// row and back to row 0: about 2 * n_rows - start row visits.  Shorter chains are mostly noise
+// triplets that stop after a few rows.  The order only changes which lane builds which
+// tracklet when; every tracklet's result is the same.
+// ---------------------------------------------------------------------------------------------
+__device__ __forceinline__ int work_key(const DevConst &c, int packed)
+{
+    const int len = (packed >> 8) & 0xff, r0 = packed & 0xff;
+    return len >= 4 ? 2 * c.nr - r0 + 1 : 0;       // 0 .. 2 nr + 1 < kOrderBuckets
+}
+
+__global__ void __launch_bounds__(256) k_order_hist(const DevConst c, const Workspace w)
+{
+    __shared__ int h[kOrderBuckets];
+    for (int i = threadIdx.x; i < kOrderBuckets; i += blockDim.x) h[i] = 0;
+    __syncthreads();
+    const int T = min(w.counters[CNT_STARTS], (int)w.tcap);
+    for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < T; t += gridDim.x * blockDim.x)
+        atomicAdd(&h[work_key(c, w.starts[t].w)], 1);
+    __syncthreads();
+    for (int i = threadIdx.x; i < kOrderBuckets; i += blockDim.x)
+        if (h[i]) atomicAdd(&w.buckets[i], h[i]);
+}
+
+// Exclusive scan of the buckets in descending key order; the cursors start at the offsets.
+__global__ void __launch_bounds__(kOrderBuckets) k_order_scan(const Workspace w)
+{
+    __shared__ int sh[kOrderBuckets / 32 + 1];
+    const int i = threadIdx.x;                      // bucket kOrderBuckets - 1 - i
+    const int v = w.buckets[kOrderBuckets - 1 - i];
+    const int lane = i & 31, warp = i >> 5;
+    const int inc = warp_incl_scan(v);
+    if (lane == 31) sh[warp] = inc;
+    __syncthreads();
+    if (warp == 0) {
+        const int nw = kOrderBuckets / 32;
+        const int x = lane < nw ? sh[lane] : 0;
+        const int xi = warp_incl_scan(x);
+        if (lane < nw) sh[lane] = xi - x;
+    }
+    __syncthreads();
+    w.buckets[kOrderBuckets + kOrderBuckets - 1 - i] = sh[warp] + inc - v;
+}
+
+__global__ void __launch_bounds__(256) k_order_scatter(const DevConst c, const Workspace w)
+{
+    const int T = min(w.counters[CNT_STARTS], (int)w.tcap);
+    for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < T; t += gridDim.x * blockDim.x) {
+        const int pos = atomicAdd(&w.buckets[kOrderBuckets + work_key(c, w.starts[t].w)], 1);
+        w.order[pos] = t;
+    }
+}
+
+// 128 threads and 6 resident CTAs per SM: 80 registers without spills (measured fastest)
+__global__ void __launch_bounds__(128, 6)
 k_construct(const DevConst c, const Workspace w)
 {
     const int T = min(__ldg(&w.counters[CNT_STARTS]), (int)w.tcap);
@@ -273,8 +327,9 @@ k_construct(const DevConst c, const Workspace w)
     int visits = 0, cands = 0;
     while (true) {
         if (phase == 0) {
-            t = atomicAdd(&w.counters[CNT_QUEUE], 1);
-            if (t >= T) break;
+            const int q = atomicAdd(&w.counters[CNT_QUEUE], 1);
+            if (q >= T) break;
+            t = w.order[q];
             const int4 sd = w.starts[t];
             sec = sd.w >> 16;
             const int len = (sd.w >> 8) & 0xff;
@@ -294,7 +349,11 @@ k_construct(const DevConst c, const Workspace w)
             rlast = -1;
             miss = 0;
         }
-        // one row visit
+        // one row visit; the row's search record is loaded first so that its latency overlaps
+        // the transport arithmetic
+        const int unit = sec * c.nr + r;
+        const int4 rg = __ldg(&w.rgi[unit]);
+        const float4 gr = __ldg(&w.grid[unit]);
         const float xr = c.row_x[r];
         KF pr = st;
         bool stop = false;
@@ -306,7 +365,7 @@ k_construct(const DevConst c, const Workspace w)
             visits++;
             const Gain g = residual_cov_inv(pr, c);
             float chi2 = 0.0f;
-            const int b = search_row(c, w, sec * c.nr + r, pr, g, chi2, cands);
+            const int b = search_row(c, w, rg, gr, pr, g, chi2, cands);
             if (b >= 0 && chi2 <= c.chi2max) {
                 const float2 q = __ldg(w.yz + b);
                 if (phase == 2) {
@@ -400,8 +459,13 @@ int launch_construct(const DevConst &c, const Workspace &w, const LaunchCfg &lc,
         cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_construct, lc.construct_block, 0);
         per_sm = occ > 0 ? occ : 1;
     }
+    cudaMemsetAsync(w.buckets, 0, kOrderBuckets * sizeof(int32_t), s);
+    const int og = lc.num_sms * 2;
+    k_order_hist<<<og, 256, 0, s>>>(c, w);
+    k_order_scan<<<1, kOrderBuckets, 0, s>>>(w);
+    k_order_scatter<<<og, 256, 0, s>>>(c, w);
     k_construct<<<lc.num_sms * per_sm, lc.construct_block, 0, s>>>(c, w);
-    return 1;
+    return 4;
 }
 
 }  // namespace tpc

@@ -54,7 +54,10 @@ k_ingest(const DevConst c, const Workspace w, const float *__restrict__ yin, con
             if (ymax > ymin) idy = (float)ny / (ymax - ymin);
             if (zmax > zmin) idz = (float)nz / (zmax - zmin);
         }
-        if (lane == 0) w.grid[u] = make_float4(ymin, zmin, idy, idz);
+        if (lane == 0) {
+            w.grid[u] = make_float4(ymin, zmin, idy, idz);
+            if (w.rgi) w.rgi[u] = make_int4(s_off, cell_off, ny, nz);
+        }
         for (int j = lane; j < nc; j += 32) hist[j] = 0;
         __syncwarp();
         for (int i = lane; i < n; i += 32) {

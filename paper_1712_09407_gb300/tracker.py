@@ -77,6 +77,7 @@ EXPORTS = {
                                      P(c_void_p)]),
     "tpc_result_sync_counts": (c_int, [c_void_p, P(c_int64), P(c_int64)]),
     "tpc_result_get": (c_int, [c_void_p, P(tpc_track_view)]),
+    "tpc_result_ready": (c_int, [c_void_p]),
     "tpc_result_copy_to_host": (c_int, [c_void_p] + [c_void_p] * 11),
     "tpc_result_release": (None, [c_void_p]),
     "tpc_tracker_destroy": (None, [c_void_p]),
@@ -204,6 +205,10 @@ def tpc_result_sync_counts(res):
     return s, m.value, h.value
 
 
+def tpc_result_ready(res) -> int:
+    return lib().tpc_result_ready(res)
+
+
 def tpc_result_get(res) -> tpc_track_view:
     v = tpc_track_view()
     _check(lib().tpc_result_get(res, ctypes.byref(v)), "tpc_result_get")
@@ -303,6 +308,12 @@ class Result:
             raise TrackerError(s, "event %d sector %d stage %s" % (ev, sec, STAGES.get(stage, stage)))
         self.n_tracks, self.n_hits = m, h
         return m, h
+
+    def ready(self) -> bool:
+        s = tpc_result_ready(self.handle)
+        if s < 0:
+            raise TrackerError(-s, "tpc_result_ready")
+        return s == 1
 
     def views(self) -> dict:
         if self.n_tracks is None:
