@@ -14,6 +14,7 @@ arm of this build) on the host cores instead.
 from __future__ import annotations
 
 import argparse
+import collections
 import hashlib
 import json
 import os
@@ -38,7 +39,7 @@ CONSTRUCT_SRC = os.path.join(ROOT, "paper_1712_09407_gb300", "csrc", "k_construc
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--steps", type=int, default=400)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -46,6 +47,8 @@ def parse():
     ap.add_argument("--workload", default="central", choices=["central", "batch"],
                     help="central: the metric's workload (default); batch: 64 events per call vs one at a time")
     ap.add_argument("--batch-events", type=int, default=64)
+    ap.add_argument("--inflight", type=int, default=2, help="central events on the device at once (one stream each)")
+    ap.add_argument("--resident", type=int, default=8, help="distinct resident central events (> L2 together)")
     return ap.parse_args()
 
 
@@ -162,7 +165,7 @@ def traffic_for_current_kernel():
 # ------------------------------------------------------------------------------------------------
 # CPU oracle legs
 # ------------------------------------------------------------------------------------------------
-def oracle_timing(ev, min_seconds=10.0, max_runs=5, min_runs=1):
+def oracle_timing(ev, min_seconds=10.0, max_runs=60, min_runs=1):
     import oracle
     cfg = oracle.config_for(ev.geometry)
     times = []
@@ -222,21 +225,32 @@ def run_ours(args):
     from paper_1712_09407_gb300 import eventgen
     from paper_1712_09407_gb300.tracker import Tracker
 
-    ev = eventgen.config_event(2, event=replica_event(rank))   # one replica per GPU, its own event
-    tr = Tracker.for_geometry(ev.geometry)
-    tr.reserve(ev.n, 1)
-    stream = torch.cuda.Stream()
-    y = torch.from_numpy(ev.y).cuda()
-    z = torch.from_numpy(ev.z).cuda()
-    row = torch.from_numpy(ev.row).cuda()
+    # Resident inputs: `resident` different central-like events (about 30 MB each, together more
+    # than the 129 MB L2), generated in parallel, copied to HBM before any timing.
+    from paper_1712_09407_gb300.serving import event_pool
+    first_event = replica_event(rank) * args.resident
+    pool = event_pool(args.resident, cfg=2, first_event=first_event)
+    import types
+    ev = types.SimpleNamespace(geometry=eventgen.Geometry(), y=pool[0][0].numpy(), z=pool[0][1].numpy(),
+                               row=pool[0][2].numpy(), counts=pool[0][3], n=pool[0][4])   # first resident event
+    dev = [(p[0].cuda(), p[1].cuda(), p[2].cuda(), p[3], p[4]) for p in pool]
+    n_mean = float(np.mean([p[4] for p in pool]))
+    trackers = [Tracker.for_geometry(ev.geometry) for _ in range(args.inflight)]
+    for t in trackers:
+        t.reserve(max(p[4] for p in pool), 1)
+    tr = trackers[0]
+    streams = [torch.cuda.Stream() for _ in range(args.inflight)]
+    stream = streams[0]
     flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
     torch.cuda.synchronize()
 
-    with torch.cuda.stream(stream):
-        for _ in range(args.warmup):
-            r = tr.track(y, z, row, ev.counts, stream=stream)
-            r.sync()
-            r.release()
+    for i, t in enumerate(trackers):
+        with torch.cuda.stream(streams[i]):
+            for k in range(args.warmup):
+                d = dev[k % len(dev)]
+                r = t.track(d[0], d[1], d[2], d[3], stream=streams[i])
+                r.sync()
+                r.release()
 
     def barrier():
         torch.cuda.synchronize()
@@ -244,49 +258,87 @@ def run_ours(args):
             torch.distributed.barrier()
         torch.cuda.synchronize()
 
-    tr.set_timing(True)
+    # ---- timed region 1 (the value): a stream of central-like events, `inflight` of them on the
+    # device at once (one tracker and stream each), inputs larger than L2 so no flush is needed
+    for t in trackers:
+        t.set_timing(True)
     clocks = ClockSampler(local)
     clocks.start()
     barrier()
     t_wall = time.perf_counter()
-    starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
-    ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
-    stage_ms = np.zeros(7)
+    t_start = torch.cuda.Event(enable_timing=True)
+    t_ends = [torch.cuda.Event(enable_timing=True) for _ in streams]
+    t_start.record(streams[0])
+    for s_ in streams[1:]:
+        s_.wait_event(t_start)
+    results = collections.deque()
     launches = 0
-    stats = None
-    results = []
-    with torch.cuda.stream(stream):
-        for k in range(args.steps):
-            flush.fill_(float(k))                      # evict L2 (not timed)
-            starts[k].record(stream)
-            results.append(tr.track(y, z, row, ev.counts, stream=stream))
-            ends[k].record(stream)
+    tracks = []
+
+    def retire(r):
+        nonlocal launches
+        r.sync()                                       # host waits on an older call; the device keeps going
+        launches += r.stats()["kernel_launches"]
+        tracks.append(r.n_tracks)
+        r.release()
+
+    for k in range(args.steps):
+        i = k % args.inflight
+        d = dev[k % len(dev)]
+        with torch.cuda.stream(streams[i]):
+            results.append(trackers[i].track(d[0], d[1], d[2], d[3], stream=streams[i]))
+        if len(results) > 4 * args.inflight:
+            retire(results.popleft())
+    for e, s_ in zip(t_ends, streams):
+        e.record(s_)
     barrier()
     wall = time.perf_counter() - t_wall
     clk = clocks.stop()
+    while results:
+        retire(results.popleft())
+    total_s = reduce_max(max(t_start.elapsed_time(e) for e in t_ends) / 1e3, world, "cuda")
+    value = replica_throughput(total_s, args.steps, world)
+
+    # ---- timed region 2 (per-event latency and the per-kernel roofline): one event at a time on
+    # one stream, L2 flushed (untimed) before each step
+    n_serial = min(args.steps, 40)
+    starts = [torch.cuda.Event(enable_timing=True) for _ in range(n_serial)]
+    ends = [torch.cuda.Event(enable_timing=True) for _ in range(n_serial)]
+    stage_ms = np.zeros(7)
+    stats_all = []
+    results = []
+    barrier()
+    with torch.cuda.stream(stream):
+        for k in range(n_serial):
+            d = dev[k % len(dev)]
+            flush.fill_(float(k))
+            starts[k].record(stream)
+            results.append(tr.track(d[0], d[1], d[2], d[3], stream=stream))
+            ends[k].record(stream)
+    barrier()
     for r in results:
         r.sync()
-        stats = r.stats()
-        stage_ms += np.array(stats["ms"])
-        launches += stats["kernel_launches"]
+        st = r.stats()
+        stats_all.append(st)
+        stage_ms += np.array(st["ms"])
         r.release()
     del results
     step_ms = [s.elapsed_time(e) for s, e in zip(starts, ends)]
-    total_s = reduce_max(sum(step_ms) / 1e3, world, "cuda")
-    value = replica_throughput(total_s, args.steps, world)
-    tr.set_timing(False)
+    serial = {"events_per_s": n_serial / (sum(step_ms) / 1e3), "ms_per_event": float(np.mean(step_ms)), "steps": n_serial,
+              "ms_per_event_p50": float(np.median(step_ms)), "l2": "flushed before every event (512 MB write, untimed)"}
+    stats = {k: int(np.mean([s[k] for s in stats_all])) for k in ("row_visits", "candidates", "tracklets")}
+    for t in trackers:
+        t.set_timing(False)
 
     # ---- end to end through the host-buffer entry point
     e2e = None
     if not args.no_e2e:
-        hy = torch.from_numpy(ev.y).pin_memory()
-        hz = torch.from_numpy(ev.z).pin_memory()
-        hr = torch.from_numpy(ev.row).pin_memory()
+        hy, hz, hr = pool[0][0], pool[0][1], pool[0][2]          # pinned host copies
         bufs = None
         times = []
         h2d = d2h = 0
         with torch.cuda.stream(stream):
-            for k in range(args.warmup + args.steps):
+            for k in range(args.warmup + min(args.steps, 40)):
                 flush.fill_(float(k))
                 torch.cuda.synchronize()
                 t0 = time.perf_counter()
@@ -314,7 +366,7 @@ def run_ours(args):
     if rank != 0:
         return 0
     names = ["setup", "ingest", "neighbours", "evolution", "construction", "selection", "output"]
-    mean_stage = stage_ms / args.steps
+    mean_stage = stage_ms / n_serial
     stages = {n: round(float(v), 4) for n, v in zip(names, mean_stage)}
     peak, peak_kind = measured_peaks()
     cb = construct_bytes(stats)
@@ -324,17 +376,19 @@ def run_ours(args):
     roof = {"kernel": "k_construct (A5 tracklet construction)", "bound": "hbm", "achieved": achieved,
             "peak": peak, "unit": "GB/s", "frac": achieved / peak, "peak_source": peak_kind + " (hbm_gbs)",
             "traffic": traffic, "algorithmic_bytes": cb, "launch_ms": con_ms,
-            "units": {"row_visits": stats["row_visits"], "tracklets": stats["tracklets"],
-                      "candidates": stats["candidates"]}}
+            "timed_in": "timed region 2 (one event at a time)", "units": stats}
     if tnote:
         roof["traffic_note"] = tnote
     line = {"metric": METRIC, "value": value, "unit": "events/s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": 1e3 * total_s / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-            "config": {"workload": WORKLOAD, "clusters_per_event": ev.n,
-                       "l2": "flushed before every step (512 MB write, untimed)",
+            "config": {"workload": WORKLOAD, "resident_events": args.resident,
+                       "clusters_per_event": int(round(n_mean)), "inflight_events": args.inflight,
+                       "l2": "inputs larger than L2 (%d resident events, %.0f MB); no flush" % (
+                           args.resident, args.resident * n_mean * 9 / 1e6),
                        "parallelism": "replicas" if world > 1 else "single GPU"},
-            "clusters_per_s": value * ev.n, "tracks_per_event": stats["tracks"], "stages_ms": stages,
+            "clusters_per_s": value * n_mean, "tracks_per_event": int(np.mean(tracks)),
+            "one_event_at_a_time": serial, "stages_ms": stages,
             "gpu_launches": launches, "e2e": e2e, "roofline": roof, "clocks": clk,
             "wall_s_timed_region": wall}
     if world == 1 and not args.no_cpu_baseline:

@@ -293,7 +293,7 @@ typedef struct {
     const int32_t *orig;           /* [n_slots] input index of each slot */
     const int32_t *up_raw, *dn_raw;/* [n_slots] A2 links (slots, -1 none) */
     const int32_t *up, *dn;        /* [n_slots] A3 kept links */
-    const int32_t *starts;         /* [n_tracklets * 4] first, middle, last slot, (sector << 16) | (chain length << 8) | row */
+    const int32_t *starts;         /* [n_tracklets * 4] first slot, -1, -1, (sector << 16) | (chain length, counted up to 4 or min_chain, << 8) | row */
     const int32_t *tl_nhits;       /* [capacity] */
     const int32_t *tl_hits;        /* [capacity * n_rows] slots, outer to inner */
     const float *tl_par;           /* [5 * capacity] component-major */

@@ -68,7 +68,7 @@ struct Workspace {
     int32_t *up_raw, *dn_raw, *up, *dn;
     unsigned long long *ckey;   // A6 claims
     // per tracklet
-    int4 *starts;          // {first, mid, last, (sector << 16) | (chain length << 8) | row}
+    int4 *starts;          // {first, -1, -1, (sector << 16) | (chain length up to max(4, min_chain) << 8) | row}
     int32_t *order;        // tracklets in the order the constructor takes them (longest expected first)
     int32_t *buckets;      // [kOrderBuckets * 2] histogram / cursors of the ordering sort
     int32_t *tl_n;

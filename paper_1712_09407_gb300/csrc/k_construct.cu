@@ -332,9 +332,16 @@ k_construct(const DevConst c, const Workspace w)
             t = w.order[q];
             const int4 sd = w.starts[t];
             sec = sd.w >> 16;
-            const int len = (sd.w >> 8) & 0xff;
             const int r0 = sd.w & 0xff;
-            const float2 q0 = w.yz[sd.x], q1 = w.yz[sd.y], q2 = w.yz[sd.z];
+            // walk the chain of kept links: its length, middle and last cluster seed the fit
+            int len = 1, last = sd.x;
+            for (int nx = w.up[last]; nx >= 0 && len < c.nr; nx = w.up[nx]) {
+                last = nx;
+                len++;
+            }
+            int mid = sd.x;
+            for (int k = 0; k < (len - 1) / 2; k++) mid = w.up[mid];
+            const float2 q0 = w.yz[sd.x], q1 = w.yz[mid], q2 = w.yz[last];
             const float x3[3] = {c.row_x[r0], c.row_x[r0 + (len - 1) / 2], c.row_x[r0 + len - 1]};
             const float y3[3] = {q0.x, q1.x, q2.x};
             const float z3[3] = {q0.y, q1.y, q2.y};

@@ -180,7 +180,7 @@ __host__ __device__ __forceinline__ int staged_row_bytes(int n, int nc)
     return round16(n * 8) + round16(n * 4) + round16((nc + 1) * 4);
 }
 
-__device__ __forceinline__ void search_pairs(const DevConst &c, const RowView &U, const RowView &D, float yc,
+__device__ __noinline__ void search_pairs_full(const DevConst &c, const RowView &U, const RowView &D, float yc,
                                              float zc, float wyu, float wzu, float wyd, float wzd, float w,
                                              float gate, int &out_u, int &out_d)
 {
@@ -228,6 +228,80 @@ __device__ __forceinline__ void search_pairs(const DevConst &c, const RowView &U
     } else {
         out_u = -1;
         out_d = -1;
+    }
+}
+
+constexpr int kDList = 12;   // row k-1 candidates kept per cluster before falling back to re-scanning
+
+// Best (u, d) pair for cluster (yc, zc): the row k-1 candidates inside the window are listed once,
+// then every row k+1 candidate inside its window is paired with each of them.  More than kDList
+// row k-1 candidates (very dense rows) use search_pairs_full, which gives the same answer.
+__device__ __forceinline__ void search_pairs(const DevConst &c, const RowView &U, const RowView &D, float yc,
+                                             float zc, float wyu, float wzu, float wyd, float wzd, float w,
+                                             float gate, int &out_u, int &out_d)
+{
+    const int iy0d = cell1(yc - wyd - kBinSlack, D.ymin, D.idy, D.ny);
+    const int iy1d = cell1(yc + wyd + kBinSlack, D.ymin, D.idy, D.ny);
+    const int iz0d = cell1(zc - wzd - kBinSlack, D.zmin, D.idz, D.nz);
+    const int iz1d = cell1(zc + wzd + kBinSlack, D.zmin, D.idz, D.nz);
+    float dly[kDList], dlz[kDList];
+    int dlj[kDList];
+    int nd = 0;
+    bool over = false;
+    for (int izd = iz0d; izd <= iz1d; izd++) {
+        const int ad = D.cell[izd * D.ny + iy0d], ed = D.cell[izd * D.ny + iy1d + 1];
+        for (int jd = ad; jd < ed; jd++) {
+            const float2 pd = D.yz[jd];
+            if (!(fabsf(pd.x - yc) <= wyd && fabsf(pd.y - zc) <= wzd)) continue;
+            if (nd < kDList) {
+                dly[nd] = pd.x;
+                dlz[nd] = pd.y;
+                dlj[nd] = jd;
+                nd++;
+            } else {
+                over = true;
+            }
+        }
+    }
+    if (over) {
+        search_pairs_full(c, U, D, yc, zc, wyu, wzu, wyd, wzd, w, gate, out_u, out_d);
+        return;
+    }
+    out_u = -1;
+    out_d = -1;
+    if (nd == 0) return;
+    const int iy0u = cell1(yc - wyu - kBinSlack, U.ymin, U.idy, U.ny);
+    const int iy1u = cell1(yc + wyu + kBinSlack, U.ymin, U.idy, U.ny);
+    const int iz0u = cell1(zc - wzu - kBinSlack, U.zmin, U.idz, U.nz);
+    const int iz1u = cell1(zc + wzu + kBinSlack, U.zmin, U.idz, U.nz);
+    int bu = -1, bd = -1, bou = 0, bod = 0;
+    float best = 0.0f;
+    for (int izu = iz0u; izu <= iz1u; izu++) {
+        const int au = U.cell[izu * U.ny + iy0u], eu = U.cell[izu * U.ny + iy1u + 1];
+        for (int ju = au; ju < eu; ju++) {
+            const float2 pu = U.yz[ju];
+            if (!(fabsf(pu.x - yc) <= wyu && fabsf(pu.y - zc) <= wzu)) continue;
+            const int ou = U.orig[ju];
+            for (int k = 0; k < nd; k++) {
+                // residual of c from the chord d -> u, evaluated at x_k (same order as the oracle)
+                const float dy = (yc - dly[k]) - (pu.x - dly[k]) * w;
+                const float dz = (zc - dlz[k]) - (pu.y - dlz[k]) * w;
+                const float sc = dy * dy * c.isy2 + dz * dz * c.isz2;
+                if (bu >= 0 && sc > best) continue;
+                const int od = D.orig[dlj[k]];
+                if (bu < 0 || sc < best || ou < bou || (ou == bou && od < bod)) {
+                    best = sc;
+                    bu = ju;
+                    bd = dlj[k];
+                    bou = ou;
+                    bod = od;
+                }
+            }
+        }
+    }
+    if (bu >= 0 && best <= gate) {
+        out_u = U.s_off + bu;
+        out_d = D.s_off + bd;
     }
 }
 
@@ -339,7 +413,7 @@ int launch_neighbours(const DevConst &c, const Workspace &w, int64_t R, int smem
 // ============================================================================================
 // A3 evolution + A4 start hits.  A link survives only if it is reciprocal.  A start hit has a
 // kept up link, no kept down link and a chain of >= min_chain clusters; its record holds the
-// first, middle and last cluster of the chain (the seed points of A5).
+// chain's first cluster and its length counted up to max(min_chain, 4).
 // ============================================================================================
 __global__ void __launch_bounds__(256) k_evolve(const DevConst c, const Workspace w, int64_t R)
 {
@@ -352,7 +426,7 @@ __global__ void __launch_bounds__(256) k_evolve(const DevConst c, const Workspac
         for (int i0 = 0; i0 < n; i0 += blockDim.x) {
             const int i = i0 + threadIdx.x;
             const bool v = i < n;
-            int first = -1, mid = -1, last = -1, clen = 0;
+            int first = -1, clen = 0;
             bool is_start = false;
             if (v) {
                 const int cl = m.z + i;
@@ -362,8 +436,12 @@ __global__ void __launch_bounds__(256) k_evolve(const DevConst c, const Workspac
                 w.up[cl] = upk;
                 w.dn[cl] = dnk;
                 if (upk >= 0 && dnk < 0) {
+                    // chain length, counted only as far as the start test and the work order need
+                    // (min_chain, and >= 4 for the constructor's ordering key); the constructor walks
+                    // the whole chain for its seed
+                    const int need = c.min_chain > 4 ? c.min_chain : 4;
                     int len = 1, t = cl;
-                    for (int k = 0; k < c.nr; k++) {
+                    while (len < need) {
                         const int nx = w.up_raw[t];
                         if (nx < 0 || w.dn_raw[nx] != t) break;
                         t = nx;
@@ -373,10 +451,6 @@ __global__ void __launch_bounds__(256) k_evolve(const DevConst c, const Workspac
                         is_start = true;
                         clen = len;
                         first = cl;
-                        last = t;
-                        int mm = cl;
-                        for (int k = 0; k < (len - 1) / 2; k++) mm = w.up_raw[mm];
-                        mid = mm;
                     }
                 }
             }
@@ -387,7 +461,7 @@ __global__ void __launch_bounds__(256) k_evolve(const DevConst c, const Workspac
             if (is_start) {
                 const int slot = base + __popc(mask & lanemask_lt());
                 if (slot < w.tcap) {
-                    w.starts[slot] = make_int4(first, mid, last, (sec << 16) | (clen << 8) | r);
+                    w.starts[slot] = make_int4(first, -1, -1, (sec << 16) | (clen << 8) | r);
                 } else {
                     set_error(w.err, TPC_ERR_CAPACITY, (int)u, c, TPC_STAGE_EVOLUTION);
                 }

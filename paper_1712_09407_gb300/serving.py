@@ -242,13 +242,13 @@ def _gen(args):
     return ev.y, ev.z, ev.row, ev.counts
 
 
-def event_pool(n_events, cfg=3, workers=8):
+def event_pool(n_events, cfg=3, workers=8, first_event=0):
     """Pre-generated events (drawn with replacement during a run), pinned in host memory."""
     import concurrent.futures as cf
     import multiprocessing as mp
     import torch
     with cf.ProcessPoolExecutor(max_workers=workers, mp_context=mp.get_context("spawn")) as ex:
-        evs = list(ex.map(_gen, [(cfg, i) for i in range(n_events)]))
+        evs = list(ex.map(_gen, [(cfg, first_event + i) for i in range(n_events)]))
     pool = []
     for y, z, row, counts in evs:
         pool.append((torch.from_numpy(y).pin_memory(), torch.from_numpy(z).pin_memory(),
