@@ -99,8 +99,12 @@ typedef struct {
     float bin_occupancy;       /* target clusters per grid cell (>0) */
     int neighbours_block;      /* threads per CTA of the neighbours finder (multiple of 32, <= 256) */
     int construct_block;       /* threads per CTA of the tracklet constructor (multiple of 32, <= 128) */
-    int construct_ctas_per_sm; /* persistent CTAs per SM of the constructor (0 = occupancy limit) */
+    int construct_ctas_per_sm; /* persistent CTAs per SM of the work-queue constructor (0 = occupancy limit) */
+    int construct_mode;        /* 0: one lane per tracklet from a work queue; 1: per-sector row sweep with rows
+                                  staged in shared memory.  Same visits, same arithmetic, same results. */
     int stage_rows;            /* 1: stage rows k-1, k+1 into shared memory with bulk copies */
+    int tracklet_capacity;     /* 0: n/4 + 64 per call; > 0: store at most this many tracklets (a capacity
+                                  knob: more start hits make the call fail with TPC_ERR_CAPACITY) */
 } tpc_tuning;
 
 typedef struct tpc_tracker tpc_tracker;
@@ -207,8 +211,10 @@ int tpc_result_copy_to_host(tpc_result *res, float *par, float *cov, float *x_re
  * NULL is ignored. */
 void tpc_result_release(tpc_result *res);
 
-/* Destroy a tracker after its outstanding work finishes.  NULL is ignored.
- * Results created by the tracker must be released first. */
+/* Destroy a tracker after its outstanding work finishes; its device workspace is freed at
+ * once.  Results it created that the caller still holds must still be released with
+ * tpc_result_release (the last release frees the tracker's remaining host state).  NULL
+ * and repeated calls are ignored. */
 void tpc_tracker_destroy(tpc_tracker *tr);
 
 /* Static text for a status code; never NULL. */
@@ -233,6 +239,12 @@ typedef struct {
     int64_t tracks;                /* output tracks */
     int64_t hits;                  /* output clusters */
 } tpc_call_stats;
+
+/* Host-side fault injection for failure tests; no GPU fault is involved.  what = 0: off;
+ * 1: the neighbours finder's shared-memory staging of sector 0's middle row waits for 16
+ * bytes that are never sent, so its bounded wait (1 s of device time) expires and the call reports
+ * TPC_ERR_TIMEOUT with stage TPC_STAGE_NEIGHBOURS.  Returns TPC_ERR_INVALID_ARG otherwise. */
+int tpc_tracker_inject(tpc_tracker *tr, int what);
 
 /* Enable (1) or disable (0) per-stage event timing for the following calls. */
 int tpc_tracker_set_timing(tpc_tracker *tr, int enable);

@@ -67,6 +67,8 @@ struct tpc_tracker {
     std::vector<int4> meta;
     std::vector<int2> dims;
     std::vector<tpc_result *> free_results;   // released results, reused without new pinned allocations
+    int64_t live_results = 0;                 // results handed out and not yet released
+    bool destroyed = false;                   // tpc_tracker_destroy was called; delete at the last release
     // last call
     int64_t last_units = 0, last_slots = 0, last_n = 0;
     bool timing = false;
@@ -155,7 +157,9 @@ extern "C" void tpc_tuning_default(tpc_tuning *t)
     t->neighbours_block = 256;
     t->construct_block = 128;
     t->construct_ctas_per_sm = 10;
+    t->construct_mode = 0;
     t->stage_rows = 1;
+    t->tracklet_capacity = 0;
 }
 
 extern "C" const char *tpc_status_string(int s)
@@ -252,7 +256,8 @@ extern "C" int tpc_tracker_set_tuning(tpc_tracker *tr, const tpc_tuning *t)
     if (!tr || !t) return TPC_ERR_INVALID_ARG;
     if (!(t->bin_occupancy >= 0.5f) || t->neighbours_block < 32 || t->neighbours_block > 256 ||
         t->neighbours_block % 32 || t->construct_block < 32 || t->construct_block > 128 ||
-        t->construct_block % 32 || t->construct_ctas_per_sm < 0)
+        t->construct_block % 32 || t->construct_ctas_per_sm < 0 || t->construct_mode < 0 || t->construct_mode > 1 ||
+        t->tracklet_capacity < 0)
         return TPC_ERR_INVALID_ARG;
     tr->tuning = *t;
     return TPC_OK;
@@ -292,6 +297,8 @@ static size_t carve(tpc_tracker *tr, const WsSizes &s, Alloc &a)
     w.starts = a.take<int4>(s.T);
     w.order = a.take<int32_t>(s.T);
     w.buckets = a.take<int32_t>(2 * kOrderBuckets);
+    w.sw_sec = a.take<int32_t>(2 * (s.R / tr->n_rows) + 64);
+    w.sw_chunks = a.take<int4>(s.T / 32 + s.R / tr->n_rows + 64);
     w.tl_n = a.take<int32_t>(s.T);
     w.tl_hits = a.take<int32_t>(s.T * tr->n_rows);
     w.tl_par = a.take<float>(5 * s.T);
@@ -313,6 +320,7 @@ static size_t carve(tpc_tracker *tr, const WsSizes &s, Alloc &a)
     w.pcap = s.P;
     w.ccap = s.C;
     w.tcap = s.T;
+    w.tlim = s.T;
     w.rcap = s.R;
     w.wcap = s.W;
     return a.used;
@@ -515,7 +523,9 @@ static int run(tpc_tracker *tr, const float *y, const float *z, const uint8_t *r
     }
     res->timed = timed;
     res->n_clusters = n_total;
-    const Workspace &w = tr->w;
+    Workspace wk = tr->w;
+    if (tr->tuning.tracklet_capacity > 0 && tr->tuning.tracklet_capacity < wk.tcap) wk.tlim = tr->tuning.tracklet_capacity;
+    const Workspace &w = wk;
     if (R > 0) {
         TPC_CUDA(cudaMemcpyAsync(w.meta, sg.meta, R * sizeof(int4), cudaMemcpyHostToDevice, st));
         TPC_CUDA(cudaMemcpyAsync(w.dims, sg.dims, R * sizeof(int2), cudaMemcpyHostToDevice, st));
@@ -531,6 +541,7 @@ static int run(tpc_tracker *tr, const float *y, const float *z, const uint8_t *r
     lc.neighbours_block = tr->tuning.neighbours_block;
     lc.construct_block = tr->tuning.construct_block;
     lc.construct_ctas_per_sm = tr->tuning.construct_ctas_per_sm;
+    lc.construct_mode = tr->tuning.construct_mode;
     lc.stage_rows = tr->tuning.stage_rows;
     lc.neighbours_smem_max = smem;
 
@@ -545,7 +556,8 @@ static int run(tpc_tracker *tr, const float *y, const float *z, const uint8_t *r
     mark(3);
     launches += launch_evolve(tr->dc, w, R, st);
     mark(4);
-    launches += launch_construct(tr->dc, w, lc, st);
+    launches += lc.construct_mode == 1 ? launch_construct_sweep(tr->dc, w, (int)(R / nr), lc, st)
+                                       : launch_construct(tr->dc, w, lc, st);
     mark(5);
     launches += launch_select(tr->dc, w, n_total, lc, st);
     mark(6);
@@ -557,6 +569,7 @@ static int run(tpc_tracker *tr, const float *y, const float *z, const uint8_t *r
     TPC_CUDA(cudaEventRecord(res->done, st));
     TPC_CUDA(cudaEventRecord(tr->ws_done, st));
     tr->ws_used = true;
+    tr->live_results++;
     tr->last_units = R;
     tr->last_slots = s_off;
     tr->last_n = n_total;
@@ -571,6 +584,7 @@ extern "C" int tpc_track_batch(tpc_tracker *tr, const float *y, const float *z, 
     if (!tr || !out || !counts || n_events < 1 || n_total < 0) return TPC_ERR_INVALID_ARG;
     *out = nullptr;
     std::lock_guard<std::mutex> g(tr->mu);
+    if (tr->destroyed) return TPC_ERR_STATE;
     return run(tr, y, z, row, counts, n_events, n_total, (cudaStream_t)stream, out);
 }
 
@@ -587,6 +601,7 @@ extern "C" int tpc_track_event_host(tpc_tracker *tr, const float *y, const float
     if (n > 0 && (!y || !z || !row)) return TPC_ERR_INVALID_ARG;
     *out = nullptr;
     std::lock_guard<std::mutex> g(tr->mu);
+    if (tr->destroyed) return TPC_ERR_STATE;
     cudaStream_t st = (cudaStream_t)stream;
     if (n > tr->in_cap) {
         if (tr->in_base) {
@@ -688,16 +703,25 @@ extern "C" int tpc_result_copy_to_host(tpc_result *r, float *par, float *cov, fl
     return TPC_OK;
 }
 
+static void free_tracker(tpc_tracker *tr);
+
 extern "C" void tpc_result_release(tpc_result *r)
 {
     if (!r) return;
     if (r->dev) cudaFreeAsync(r->dev, r->stream);
     r->dev = nullptr;
     if (r->done) cudaEventSynchronize(r->done);
-    std::lock_guard<std::mutex> g(r->tr->mu);
-    r->tr->bytes_results -= r->bytes;
-    r->bytes = 0;
-    r->tr->free_results.push_back(r);      // pinned counts and events are kept for the next call
+    tpc_tracker *tr = r->tr;
+    bool last = false;
+    {
+        std::lock_guard<std::mutex> g(tr->mu);
+        tr->bytes_results -= r->bytes;
+        r->bytes = 0;
+        tr->free_results.push_back(r);      // pinned counts and events are kept for the next call
+        tr->live_results--;
+        last = tr->destroyed && tr->live_results == 0;
+    }
+    if (last) free_tracker(tr);             // the tracker was destroyed while this result was alive
 }
 
 static void destroy_result(tpc_result *r)
@@ -709,20 +733,39 @@ static void destroy_result(tpc_result *r)
     delete r;
 }
 
+static void free_tracker(tpc_tracker *tr)
+{
+    for (tpc_result *r : tr->free_results) destroy_result(r);
+    tr->free_results.clear();
+    delete tr;
+}
+
 extern "C" void tpc_tracker_destroy(tpc_tracker *tr)
 {
     if (!tr) return;
     cudaDeviceSynchronize();
-    if (tr->ws_base) cudaFree(tr->ws_base);
-    if (tr->in_base) cudaFree(tr->in_base);
-    for (auto &s : tr->staging) {
-        if (s.meta) cudaFreeHost(s.meta);
-        if (s.dims) cudaFreeHost(s.dims);
-        if (s.consumed) cudaEventDestroy(s.consumed);
+    bool now = false;
+    {
+        std::lock_guard<std::mutex> g(tr->mu);
+        if (tr->destroyed) return;
+        tr->destroyed = true;
+        if (tr->ws_base) cudaFree(tr->ws_base);
+        if (tr->in_base) cudaFree(tr->in_base);
+        tr->ws_base = tr->in_base = nullptr;
+        for (auto &st : tr->staging) {
+            if (st.meta) cudaFreeHost(st.meta);
+            if (st.dims) cudaFreeHost(st.dims);
+            if (st.consumed) cudaEventDestroy(st.consumed);
+            st.meta = nullptr;
+            st.dims = nullptr;
+            st.consumed = nullptr;
+        }
+        if (tr->ws_done) cudaEventDestroy(tr->ws_done);
+        tr->ws_done = nullptr;
+        now = tr->live_results == 0;
     }
-    if (tr->ws_done) cudaEventDestroy(tr->ws_done);
-    for (tpc_result *r : tr->free_results) destroy_result(r);
-    delete tr;
+    // results still held by the caller keep the (device-free) tracker object alive until released
+    if (now) free_tracker(tr);
 }
 
 extern "C" int tpc_last_error_detail(tpc_tracker *tr, int *event, int *sector, int *stage)
@@ -733,6 +776,13 @@ extern "C" int tpc_last_error_detail(tpc_tracker *tr, int *event, int *sector, i
     if (sector) *sector = tr->last_err[ERR_SECTOR];
     if (stage) *stage = tr->last_err[ERR_STAGE];
     return tr->last_err[ERR_STATUS];
+}
+
+extern "C" int tpc_tracker_inject(tpc_tracker *tr, int what)
+{
+    if (!tr || what < 0 || what > 1) return TPC_ERR_INVALID_ARG;
+    tr->dc.inject = what;
+    return TPC_OK;
 }
 
 extern "C" int tpc_tracker_set_timing(tpc_tracker *tr, int enable)
@@ -770,6 +820,8 @@ extern "C" int tpc_tracker_debug_view(tpc_tracker *tr, tpc_debug_view *v)
     v->n_units = tr->last_units;
     v->n_slots = tr->last_slots;
     v->n_tracklets = cnt[CNT_STARTS] < w.tcap ? cnt[CNT_STARTS] : w.tcap;
+    if (tr->tuning.tracklet_capacity > 0 && v->n_tracklets > tr->tuning.tracklet_capacity)
+        v->n_tracklets = tr->tuning.tracklet_capacity;
     v->tracklet_capacity = w.tcap;
     v->unit_meta = (const int32_t *)w.meta;
     v->unit_cells = (const int32_t *)w.dims;

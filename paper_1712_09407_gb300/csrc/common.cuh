@@ -26,6 +26,7 @@ enum {
     CNT_HITS = 3,       // output hits (A7)
     CNT_VISITS = 4,     // A5 row visits (statistics)
     CNT_CANDS = 5,      // A5 clusters read inside the enumerated grid cells (statistics)
+    CNT_SW_CHUNKS = 6,  // chunks of the sector-sweep constructor
     CNT_COUNT = 8
 };
 
@@ -51,6 +52,7 @@ struct DevConst {
     int max_miss;
     int min_chain;
     int min_clusters;
+    int inject;         // host-side test hook (0 = off): 1 makes one staging wait of the neighbours finder expire
 };
 
 // Per row unit metadata (host-computed): input offset, count, sorted offset, cell offset.
@@ -71,6 +73,8 @@ struct Workspace {
     int4 *starts;          // {first, -1, -1, (sector << 16) | (chain length up to max(4, min_chain) << 8) | row}
     int32_t *order;        // tracklets in the order the constructor takes them (longest expected first)
     int32_t *buckets;      // [kOrderBuckets * 2] histogram / cursors of the ordering sort
+    int32_t *sw_sec;       // [2 * sectors] tracklets per sector, scatter cursors (sweep constructor)
+    int4 *sw_chunks;       // {sector, first position in order, count, 0} per chunk (sweep constructor)
     int32_t *tl_n;
     int32_t *tl_hits;      // [tcap * nr]
     float *tl_par;         // [5 * tcap]
@@ -88,7 +92,24 @@ struct Workspace {
     int32_t *counters;     // [CNT_COUNT]
     int32_t *err;          // [4]
     int64_t ncap, pcap, ccap, tcap, rcap, wcap;
+    int64_t tlim;          // tracklets that may be stored (<= tcap, the stride of the per-tracklet arrays)
 };
+
+// Number of tracklets of the current call that were stored.
+__device__ __forceinline__ int n_tracklets(const Workspace &w)
+{
+    const int s = w.counters[CNT_STARTS];
+    return s < (int)w.tlim ? s : (int)w.tlim;
+}
+
+// Device wall clock (ns) for waits bounded in time.
+__device__ __forceinline__ uint64_t global_ns()
+{
+    uint64_t t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+constexpr uint64_t kWaitNs = 1000000000ull;   // every device wait gives up after 1 s
 
 struct OutBuffers {
     float *par, *cov, *x, *alpha, *chi2;
@@ -156,6 +177,7 @@ struct LaunchCfg {
     int neighbours_block;
     int construct_block;
     int construct_ctas_per_sm;
+    int construct_mode;        // 0: per-lane work queue, 1: sector sweep
     int stage_rows;
     int neighbours_smem_max;   // bytes of dynamic shared memory for staged rows
 };
@@ -165,6 +187,7 @@ int launch_neighbours(const DevConst &c, const Workspace &w, int64_t R, int smem
                        cudaStream_t s);
 int launch_evolve(const DevConst &c, const Workspace &w, int64_t R, cudaStream_t s);
 int launch_construct(const DevConst &c, const Workspace &w, const LaunchCfg &lc, cudaStream_t s);
+int launch_construct_sweep(const DevConst &c, const Workspace &w, int n_sec, const LaunchCfg &lc, cudaStream_t s);
 int launch_select(const DevConst &c, const Workspace &w, int64_t n_input, const LaunchCfg &lc, cudaStream_t s);
 int launch_output(const DevConst &c, const Workspace &w, const OutBuffers &o, int64_t n_input,
                    const LaunchCfg &lc, cudaStream_t s);

@@ -9,254 +9,10 @@
 //
 // Floating-point expressions follow the same operation order as the CPU oracle's float mode
 // (the library is compiled without FMA contraction), so both evaluate identical roundings.
-#include "common.cuh"
+#include "kf.cuh"
 #include "../../include/tpcca.h"
 
 namespace tpc {
-
-struct KF {
-    float p0, p1, p2, p3, p4;
-    // lower triangle of the covariance, row-major
-    float c00, c10, c11, c20, c21, c22, c30, c31, c32, c33, c40, c41, c42, c43, c44;
-};
-
-// asin(u)/u with a fixed series, so that every float implementation of the tracker rounds the
-// same way (cluster ownership is decided by comparing weights): Maclaurin series of arcsin,
-// asin(u)/u = sum_n (2n)! / (4^n (n!)^2 (2n+1)) u^(2n), twelve terms by Horner's rule for
-// |u| <= 0.5, larger |u| reduced with asin(u) = 2 asin(u / sqrt(2 (1 + sqrt(1 - u^2)))).
-__device__ __forceinline__ float asin_ratio(float u)
-{
-    float v = u, m = 1.0f;
-    for (int k = 0; k < 3 && fabsf(v) > 0.5f; k++) {
-        v = v / sqrtf(2.0f * (1.0f + sqrtf(1.0f - v * v)));
-        m = m * 2.0f;
-    }
-    const float t = v * v;
-    float s = 0.007312526f;
-    s = s * t + 0.00839033537f;
-    s = s * t + 0.00976160914f;
-    s = s * t + 0.0115518011f;
-    s = s * t + 0.0139648439f;
-    s = s * t + 0.0173527636f;
-    s = s * t + 0.0223721582f;
-    s = s * t + 0.030381944f;
-    s = s * t + 0.0446428582f;
-    s = s * t + 0.075000003f;
-    s = s * t + 0.166666672f;
-    s = s * t + 1.0f;
-    if (m == 1.0f) return s;
-    return ((m * v) * s) / u;
-}
-
-// Exact helix transport by dx with covariance C <- F C F^T (F: Jacobian of the transport).
-__device__ __forceinline__ bool propagate(KF &s, float dx, const DevConst &c)
-{
-    const float cur = c.kB * s.p4;
-    const float s0 = s.p2;
-    const float s1 = s0 + cur * dx;
-    if (!(fabsf(s1) < c.smax)) return false;
-    const float c0 = sqrtf(1.0f - s0 * s0);
-    const float c1 = sqrtf(1.0f - s1 * s1);
-    const float A = s0 + s1;
-    const float B = c0 + c1;
-    const float tq = A / B;
-    const float dy = dx * tq;
-    float L = sqrtf(dx * dx + dy * dy);
-    if (dx < 0.0f) L = -L;
-    const float u = (cur * L) * 0.5f;
-    const float ratio = asin_ratio(u);
-    const float dS = L * ratio;
-    const float tl = s.p3;
-    const float dz = tl * dS;
-    const float BB = B * B;
-    const float F02 = dx * (2.0f * B + A * (s0 / c0 + s1 / c1)) / BB;
-    const float F04 = dx * (c.kB * dx) * (B + A * (s1 / c1)) / BB;
-    const float F24 = c.kB * dx;
-    const float g = (L != 0.0f) ? (1.0f / sqrtf(1.0f - u * u)) * (dy / L) : 0.0f;
-    const float F12 = tl * (g * F02);
-    const float F13 = dS;
-    const float F14 = tl * (g * F04 + (((cur * L) * (L * L)) / 12.0f) * c.kB);
-
-    s.p0 = s.p0 + dy;
-    s.p1 = s.p1 + dz;
-    s.p2 = s1;
-
-    // FC = F C, row by row (k ascending, zero terms dropped)
-    const float C00 = s.c00, C01 = s.c10, C02 = s.c20, C03 = s.c30, C04 = s.c40;
-    const float C11 = s.c11, C12 = s.c21, C13 = s.c31, C14 = s.c41;
-    const float C22 = s.c22, C23 = s.c32, C24 = s.c42;
-    const float C33 = s.c33, C34 = s.c43, C44 = s.c44;
-    const float FC00 = (C00 + F02 * C02) + F04 * C04;
-    const float FC02 = (C02 + F02 * C22) + F04 * C24;
-    const float FC04 = (C04 + F02 * C24) + F04 * C44;
-    const float FC10 = ((C01 + F12 * C02) + F13 * C03) + F14 * C04;
-    const float FC11 = ((C11 + F12 * C12) + F13 * C13) + F14 * C14;
-    const float FC12 = ((C12 + F12 * C22) + F13 * C23) + F14 * C24;
-    const float FC13 = ((C13 + F12 * C23) + F13 * C33) + F14 * C34;
-    const float FC14 = ((C14 + F12 * C24) + F13 * C34) + F14 * C44;
-    const float FC20 = C02 + F24 * C04;
-    const float FC21 = C12 + F24 * C14;
-    const float FC22 = C22 + F24 * C24;
-    const float FC23 = C23 + F24 * C34;
-    const float FC24 = C24 + F24 * C44;
-    // N = FC F^T, lower triangle (k ascending)
-    s.c00 = (FC00 + FC02 * F02) + FC04 * F04;
-    s.c10 = (FC10 + FC12 * F02) + FC14 * F04;
-    s.c11 = ((FC11 + FC12 * F12) + FC13 * F13) + FC14 * F14;
-    s.c20 = (FC20 + FC22 * F02) + FC24 * F04;
-    s.c21 = ((FC21 + FC22 * F12) + FC23 * F13) + FC24 * F14;
-    s.c22 = FC22 + FC24 * F24;
-    s.c30 = (C03 + C23 * F02) + C34 * F04;
-    s.c31 = ((C13 + C23 * F12) + C33 * F13) + C34 * F14;
-    s.c32 = C23 + C34 * F24;
-    // s.c33 unchanged
-    s.c40 = (C04 + C24 * F02) + C44 * F04;
-    s.c41 = ((C14 + C24 * F12) + C34 * F13) + C44 * F14;
-    s.c42 = C24 + C44 * F24;
-    // s.c43, s.c44 unchanged
-    return true;
-}
-
-struct Gain {
-    float s00, s01, s10, s11;   // inverse residual covariance
-};
-
-__device__ __forceinline__ Gain residual_cov_inv(const KF &s, const DevConst &c)
-{
-    const float S00 = s.c00 + c.sy2, S01 = s.c10, S10 = s.c10, S11 = s.c11 + c.sz2;
-    const float det = S00 * S11 - S01 * S10;
-    const float idet = 1.0f / det;
-    Gain g;
-    g.s00 = S11 * idet;
-    g.s01 = -S01 * idet;
-    g.s10 = -S10 * idet;
-    g.s11 = S00 * idet;
-    return g;
-}
-
-__device__ __forceinline__ float chi2_of(const Gain &g, float r0, float r1)
-{
-    const float t0 = g.s00 * r0 + g.s01 * r1;
-    const float t1 = g.s10 * r0 + g.s11 * r1;
-    return r0 * t0 + r1 * t1;
-}
-
-__device__ __forceinline__ void kf_update(KF &s, const Gain &g, float my, float mz)
-{
-    const float r0 = my - s.p0, r1 = mz - s.p1;
-    // K = C H^T S^-1
-    const float K00 = s.c00 * g.s00 + s.c10 * g.s10, K01 = s.c00 * g.s01 + s.c10 * g.s11;
-    const float K10 = s.c10 * g.s00 + s.c11 * g.s10, K11 = s.c10 * g.s01 + s.c11 * g.s11;
-    const float K20 = s.c20 * g.s00 + s.c21 * g.s10, K21 = s.c20 * g.s01 + s.c21 * g.s11;
-    const float K30 = s.c30 * g.s00 + s.c31 * g.s10, K31 = s.c30 * g.s01 + s.c31 * g.s11;
-    const float K40 = s.c40 * g.s00 + s.c41 * g.s10, K41 = s.c40 * g.s01 + s.c41 * g.s11;
-    s.p0 = s.p0 + (K00 * r0 + K01 * r1);
-    s.p1 = s.p1 + (K10 * r0 + K11 * r1);
-    s.p2 = s.p2 + (K20 * r0 + K21 * r1);
-    s.p3 = s.p3 + (K30 * r0 + K31 * r1);
-    s.p4 = s.p4 + (K40 * r0 + K41 * r1);
-    // C <- C - K H C (rows 0 and 1 of C are C(0, j) and C(1, j))
-    const float A0 = s.c00, A1 = s.c10, A2 = s.c20, A3 = s.c30, A4 = s.c40;   // C(0, j)
-    const float B0 = s.c10, B1 = s.c11, B2 = s.c21, B3 = s.c31, B4 = s.c41;   // C(1, j)
-    s.c00 = s.c00 - (K00 * A0 + K01 * B0);
-    s.c10 = s.c10 - (K10 * A0 + K11 * B0);
-    s.c11 = s.c11 - (K10 * A1 + K11 * B1);
-    s.c20 = s.c20 - (K20 * A0 + K21 * B0);
-    s.c21 = s.c21 - (K20 * A1 + K21 * B1);
-    s.c22 = s.c22 - (K20 * A2 + K21 * B2);
-    s.c30 = s.c30 - (K30 * A0 + K31 * B0);
-    s.c31 = s.c31 - (K30 * A1 + K31 * B1);
-    s.c32 = s.c32 - (K30 * A2 + K31 * B2);
-    s.c33 = s.c33 - (K30 * A3 + K31 * B3);
-    s.c40 = s.c40 - (K40 * A0 + K41 * B0);
-    s.c41 = s.c41 - (K40 * A1 + K41 * B1);
-    s.c42 = s.c42 - (K40 * A2 + K41 * B2);
-    s.c43 = s.c43 - (K40 * A3 + K41 * B3);
-    s.c44 = s.c44 - (K40 * A4 + K41 * B4);
-}
-
-__device__ __forceinline__ void set_seed_cov(KF &s, const DevConst &c)
-{
-    s.c00 = c.cov0[0];
-    s.c10 = 0.0f;
-    s.c11 = c.cov0[1];
-    s.c20 = s.c21 = 0.0f;
-    s.c22 = c.cov0[2];
-    s.c30 = s.c31 = s.c32 = 0.0f;
-    s.c33 = c.cov0[3];
-    s.c40 = s.c41 = s.c42 = s.c43 = 0.0f;
-    s.c44 = c.cov0[4];
-}
-
-// Circle through the (x, y) of three chain points; tan lambda from the z rise over the arc.
-__device__ __forceinline__ bool seed3(const float x[3], const float y[3], const float z[3], const DevConst &c,
-                                      KF &s)
-{
-    const float ax = x[1] - x[0], ay = y[1] - y[0];
-    const float bx = x[2] - x[0], by = y[2] - y[0];
-    const float cx = x[2] - x[1], cy = y[2] - y[1];
-    const float la = sqrtf(ax * ax + ay * ay);
-    const float lb = sqrtf(bx * bx + by * by);
-    const float lc = sqrtf(cx * cx + cy * cy);
-    const float cross = ax * by - ay * bx;
-    const float den = (la * lb) * lc;
-    if (!(den > 0.0f)) return false;
-    const float C = (2.0f * cross) / den;
-    const float sa = (C * lb) * 0.5f;
-    if (!(fabsf(sa) < 1.0f)) return false;
-    const float ca = sqrtf(1.0f - sa * sa);
-    const float sinphi = (by / lb) * ca - (bx / lb) * sa;
-    if (!(fabsf(sinphi) < c.smax)) return false;
-    const float S02 = lb * asin_ratio(sa);
-    s.p0 = y[0];
-    s.p1 = z[0];
-    s.p2 = sinphi;
-    s.p3 = (z[2] - z[0]) / S02;
-    s.p4 = (c.kB != 0.0f) ? C / c.kB : 0.0f;
-    return true;
-}
-
-// Best cluster of one row unit for a predicted state: minimum chi2 inside the window,
-// ties to the lower input index.  rg = {slot offset, cell offset, ny, nz}, gr = {ymin, zmin,
-// 1/dy, 1/dz} of the unit.  Returns the slot or -1.
-__device__ __forceinline__ int search_row(const DevConst &c, const Workspace &w, const int4 rg, const float4 gr,
-                                          const KF &pr, const Gain &g, float &chi2_out, int &ncand)
-{
-    const float wy = c.nsig * sqrtf(pr.c00 + c.sy2);
-    const float wz = c.nsig * sqrtf(pr.c11 + c.sz2);
-    const float y = pr.p0, z = pr.p1;
-    const int iy0 = cell1(y - wy - kBinSlack, gr.x, gr.z, rg.z);
-    const int iy1 = cell1(y + wy + kBinSlack, gr.x, gr.z, rg.z);
-    const int iz0 = cell1(z - wz - kBinSlack, gr.y, gr.w, rg.w);
-    const int iz1 = cell1(z + wz + kBinSlack, gr.y, gr.w, rg.w);
-    const int32_t *cell = w.cell + rg.y;
-    const float2 *yz = w.yz + rg.x;
-    int best = -1, borig = -1;       // borig: input index of the best slot, loaded on the first tie
-    float bc = 0.0f;
-    for (int iz = iz0; iz <= iz1; iz++) {
-        const int a = __ldg(cell + iz * rg.z + iy0), e = __ldg(cell + iz * rg.z + iy1 + 1);
-        ncand += e - a;
-        for (int j = a; j < e; j++) {
-            const float2 q = __ldg(yz + j);
-            if (!(fabsf(q.x - y) <= wy && fabsf(q.y - z) <= wz)) continue;
-            const float x2 = chi2_of(g, q.x - y, q.y - z);
-            if (best < 0 || x2 < bc) {
-                best = j;
-                bc = x2;
-                borig = -1;
-            } else if (x2 == bc) {
-                if (borig < 0) borig = __ldg(w.orig + rg.x + best);
-                const int o = __ldg(w.orig + rg.x + j);
-                if (o < borig) {
-                    best = j;
-                    borig = o;
-                }
-            }
-        }
-    }
-    chi2_out = bc;
-    return best < 0 ? -1 : rg.x + best;
-}
 
 // ---------------------------------------------------------------------------------------------
 // Longest-expected-first order of the tracklets (counting sort on a small key), so that the
@@ -277,7 +33,7 @@ __global__ void __launch_bounds__(256) k_order_hist(const DevConst c, const Work
     __shared__ int h[kOrderBuckets];
     for (int i = threadIdx.x; i < kOrderBuckets; i += blockDim.x) h[i] = 0;
     __syncthreads();
-    const int T = min(w.counters[CNT_STARTS], (int)w.tcap);
+    const int T = n_tracklets(w);
     for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < T; t += gridDim.x * blockDim.x)
         atomicAdd(&h[work_key(c, w.starts[t].w)], 1);
     __syncthreads();
@@ -307,7 +63,7 @@ __global__ void __launch_bounds__(kOrderBuckets) k_order_scan(const Workspace w)
 
 __global__ void __launch_bounds__(256) k_order_scatter(const DevConst c, const Workspace w)
 {
-    const int T = min(w.counters[CNT_STARTS], (int)w.tcap);
+    const int T = n_tracklets(w);
     for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < T; t += gridDim.x * blockDim.x) {
         const int pos = atomicAdd(&w.buckets[kOrderBuckets + work_key(c, w.starts[t].w)], 1);
         w.order[pos] = t;
@@ -318,7 +74,7 @@ __global__ void __launch_bounds__(256) k_order_scatter(const DevConst c, const W
 __global__ void __launch_bounds__(128, 6)
 k_construct(const DevConst c, const Workspace w)
 {
-    const int T = min(__ldg(&w.counters[CNT_STARTS]), (int)w.tcap);
+    const int T = n_tracklets(w);
     const int tcap = (int)w.tcap;
     int phase = 0;            // 0: needs a tracklet, 1: outward pass, 2: inward pass
     int t = 0, sec = 0, r = 0, rlast = -1, miss = 0, n = 0, orig0 = 0;
@@ -333,23 +89,10 @@ k_construct(const DevConst c, const Workspace w)
             const int4 sd = w.starts[t];
             sec = sd.w >> 16;
             const int r0 = sd.w & 0xff;
-            // walk the chain of kept links: its length, middle and last cluster seed the fit
-            int len = 1, last = sd.x;
-            for (int nx = w.up[last]; nx >= 0 && len < c.nr; nx = w.up[nx]) {
-                last = nx;
-                len++;
-            }
-            int mid = sd.x;
-            for (int k = 0; k < (len - 1) / 2; k++) mid = w.up[mid];
-            const float2 q0 = w.yz[sd.x], q1 = w.yz[mid], q2 = w.yz[last];
-            const float x3[3] = {c.row_x[r0], c.row_x[r0 + (len - 1) / 2], c.row_x[r0 + len - 1]};
-            const float y3[3] = {q0.x, q1.x, q2.x};
-            const float z3[3] = {q0.y, q1.y, q2.y};
             orig0 = w.orig[sd.x];
             w.tl_n[t] = 0;
             w.tl_key[t] = 0ull;
-            if (!seed3(x3, y3, z3, c, st)) continue;
-            set_seed_cov(st, c);
+            if (!seed_tracklet(c, w, sd, st)) continue;
             phase = 1;
             r = r0;
             xs = c.row_x[r0];
@@ -372,7 +115,9 @@ k_construct(const DevConst c, const Workspace w)
             visits++;
             const Gain g = residual_cov_inv(pr, c);
             float chi2 = 0.0f;
-            const int b = search_row(c, w, rg, gr, pr, g, chi2, cands);
+            const int bl = search_cells(c, w.yz + rg.x, w.orig + rg.x, w.cell + rg.y, gr, rg.z, rg.w, pr, g, chi2,
+                                        cands);
+            const int b = bl < 0 ? -1 : rg.x + bl;
             if (b >= 0 && chi2 <= c.chi2max) {
                 const float2 q = __ldg(w.yz + b);
                 if (phase == 2) {
@@ -408,40 +153,7 @@ k_construct(const DevConst c, const Workspace w)
                 }
             } else {
                 // the state sits at the innermost fitted cluster
-                const int ndf = 2 * n - 5;
-                w.tl_n[t] = n;
-                w.tl_x[t] = xs;
-                w.tl_chi2[t] = chi2sum;
-                float* P = w.tl_par;
-                P[0 * tcap + t] = st.p0;
-                P[1 * tcap + t] = st.p1;
-                P[2 * tcap + t] = st.p2;
-                P[3 * tcap + t] = st.p3;
-                P[4 * tcap + t] = st.p4;
-                float *V = w.tl_cov;
-                V[0 * tcap + t] = st.c00;
-                V[1 * tcap + t] = st.c10;
-                V[2 * tcap + t] = st.c11;
-                V[3 * tcap + t] = st.c20;
-                V[4 * tcap + t] = st.c21;
-                V[5 * tcap + t] = st.c22;
-                V[6 * tcap + t] = st.c30;
-                V[7 * tcap + t] = st.c31;
-                V[8 * tcap + t] = st.c32;
-                V[9 * tcap + t] = st.c33;
-                V[10 * tcap + t] = st.c40;
-                V[11 * tcap + t] = st.c41;
-                V[12 * tcap + t] = st.c42;
-                V[13 * tcap + t] = st.c43;
-                V[14 * tcap + t] = st.c44;
-                if (ndf >= 1) {
-                    // Section 3.1: w = n * (alpha - chi2/beta), chi2 read as chi2 per degree of freedom
-                    const float wt = (float)n * (c.alpha - (chi2sum / (float)ndf) / c.beta);
-                    w.tl_w[t] = wt;
-                    w.tl_key[t] = ((unsigned long long)ordered_bits(wt) << 32) | (unsigned)(~orig0);
-                } else {
-                    w.tl_w[t] = -INFINITY;
-                }
+                write_tracklet(c, w, t, st, xs, n, chi2sum, orig0);
                 phase = 0;
             }
         }

@@ -162,15 +162,15 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, unsigned parity)
     return ok != 0;
 }
 
-// Bounded wait on an mbarrier phase: gives up after `limit` polls.
-__device__ __forceinline__ bool mbar_wait_bounded(uint64_t *bar, unsigned parity, int limit)
+// Wait on an mbarrier phase for at most kWaitNs of device time; false if it gave up.
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t *bar, unsigned parity)
 {
-    for (int i = 0; i < limit; i++)
-        if (mbar_try_wait(bar, parity)) return true;
-    return false;
+    if (mbar_try_wait(bar, parity)) return true;
+    const uint64_t t0 = global_ns();
+    while (!mbar_try_wait(bar, parity))
+        if (global_ns() - t0 > kWaitNs) return false;
+    return true;
 }
-
-constexpr int kWaitLimit = 1 << 22;
 
 __host__ __device__ __forceinline__ int round16(int bytes) { return (bytes + 15) & ~15; }
 
@@ -310,7 +310,9 @@ k_neighbours(const DevConst c, const Workspace w, int64_t R, int smem_bytes, int
 {
     extern __shared__ __align__(16) unsigned char sm[];
     __shared__ __align__(8) uint64_t bar;
+    __shared__ int abort_flag;
     if (threadIdx.x == 0) {
+        abort_flag = 0;
         mbar_init(&bar, 1);
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
@@ -356,7 +358,11 @@ k_neighbours(const DevConst c, const Workspace w, int64_t R, int smem_bytes, int
             int32_t *sce_d = (int32_t *)p;
             if (threadIdx.x == 0) {
                 asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-                mbar_expect_tx(&bar, (unsigned)(bytes_u + bytes_d));
+                // test hook: the staging of sector 0's middle row expects 16 bytes that never come,
+                // so its bounded wait expires and the call reports TPC_ERR_TIMEOUT (no copy is left
+                // in flight)
+                const unsigned extra = (c.inject == 1 && u == c.nr / 2) ? 16u : 0u;
+                mbar_expect_tx(&bar, (unsigned)(bytes_u + bytes_d) + extra);
                 bulk_g2s(syz_u, U.yz, round16(mu.y * 8), &bar);
                 bulk_g2s(sor_u, U.orig, round16(mu.y * 4), &bar);
                 bulk_g2s(sce_u, U.cell, round16((du.x * du.y + 1) * 4), &bar);
@@ -364,11 +370,29 @@ k_neighbours(const DevConst c, const Workspace w, int64_t R, int smem_bytes, int
                 bulk_g2s(sor_d, D.orig, round16(md.y * 4), &bar);
                 bulk_g2s(sce_d, D.cell, round16((dd.x * dd.y + 1) * 4), &bar);
             }
-            if (!mbar_wait_bounded(&bar, parity, kWaitLimit)) {
-                if (threadIdx.x == 0) set_error(w.err, TPC_ERR_TIMEOUT, (int)u, c, TPC_STAGE_NEIGHBOURS);
-                mbar_wait_bounded(&bar, parity, kWaitLimit);   // let the copies land before leaving
+            // one thread does the bounded wait and the CTA agrees on the outcome before anyone
+            // leaves; then every thread passes the completed phase (acquire ordering)
+            if (threadIdx.x == 0) {
+                abort_flag = !mbar_wait_bounded(&bar, parity);
+                if (abort_flag) {
+                    set_error(w.err, TPC_ERR_TIMEOUT, (int)u, c, TPC_STAGE_NEIGHBOURS);
+                    mbar_wait_bounded(&bar, parity);   // let the copies land before leaving
+                }
+            }
+            __syncthreads();
+            if (abort_flag) {
+                // the staging gave up: this CTA writes "no link" for all its remaining clusters
+                // (so later stages only ever follow valid slots) and stages nothing more
+                for (int64_t v = u; v < R; v += gridDim.x) {
+                    const int4 mv = w.meta[v];
+                    for (int i = threadIdx.x; i < mv.y; i += blockDim.x) {
+                        w.up_raw[mv.z + i] = -1;
+                        w.dn_raw[mv.z + i] = -1;
+                    }
+                }
                 return;
             }
+            mbar_wait_bounded(&bar, parity);
             parity ^= 1u;
             U.yz = syz_u;
             U.orig = sor_u;
@@ -460,7 +484,7 @@ __global__ void __launch_bounds__(256) k_evolve(const DevConst c, const Workspac
             base = __shfl_sync(kFull, base, 0);
             if (is_start) {
                 const int slot = base + __popc(mask & lanemask_lt());
-                if (slot < w.tcap) {
+                if (slot < w.tlim) {
                     w.starts[slot] = make_int4(first, -1, -1, (sec << 16) | (clen << 8) | r);
                 } else {
                     set_error(w.err, TPC_ERR_CAPACITY, (int)u, c, TPC_STAGE_EVOLUTION);

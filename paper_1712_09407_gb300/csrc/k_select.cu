@@ -142,7 +142,7 @@ static void scan(const void *in, int32_t *out, int64_t n, const int32_t *n_dev, 
 // ---------------------------------------------------------------------------------------------
 __global__ void __launch_bounds__(256) k_claim(const DevConst c, const Workspace w)
 {
-    const int T = min(w.counters[CNT_STARTS], (int)w.tcap);
+    const int T = n_tracklets(w);
     const int lane = threadIdx.x & 31;
     const int nwarps = (gridDim.x * blockDim.x) >> 5;
     for (int t = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; t < T; t += nwarps) {
@@ -156,7 +156,7 @@ __global__ void __launch_bounds__(256) k_claim(const DevConst c, const Workspace
 
 __global__ void __launch_bounds__(256) k_count(const DevConst c, const Workspace w)
 {
-    const int T = min(w.counters[CNT_STARTS], (int)w.tcap);
+    const int T = n_tracklets(w);
     const int lane = threadIdx.x & 31;
     const int nwarps = (gridDim.x * blockDim.x) >> 5;
     for (int t = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; t < T; t += nwarps) {
@@ -199,7 +199,7 @@ int launch_select(const DevConst &c, const Workspace &w, int64_t n_input, const 
 // ---------------------------------------------------------------------------------------------
 __global__ void __launch_bounds__(256) k_rank(const Workspace w)
 {
-    const int T = min(w.counters[CNT_STARTS], (int)w.tcap);
+    const int T = n_tracklets(w);
     for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < T; t += gridDim.x * blockDim.x) {
         const int o = w.tl_inner[t];
         if (o < 0) continue;

@@ -106,6 +106,7 @@ extern "C" int tpc_find_links_noalloc(tpc_tracker *tr, const float *y, const flo
     w.dn_raw = (int32_t *)(base + kOffDn);
     w.err = (int32_t *)(base + kOffErr);
     w.pcap = kSlots;
+    w.tlim = 0;
     w.ccap = kCells;
     w.rcap = kMaxR;
 

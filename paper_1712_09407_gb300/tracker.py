@@ -42,7 +42,8 @@ class tpc_params(ctypes.Structure):
 
 class tpc_tuning(ctypes.Structure):
     _fields_ = [("bin_occupancy", c_float), ("neighbours_block", c_int), ("construct_block", c_int),
-                ("construct_ctas_per_sm", c_int), ("stage_rows", c_int)]
+                ("construct_ctas_per_sm", c_int), ("construct_mode", c_int), ("stage_rows", c_int),
+                ("tracklet_capacity", c_int)]
 
 
 class tpc_track_view(ctypes.Structure):
@@ -85,6 +86,7 @@ EXPORTS = {
     "tpc_last_error_detail": (c_int, [c_void_p, P(c_int), P(c_int), P(c_int)]),
     "tpc_tracker_debug_view": (c_int, [c_void_p, P(tpc_debug_view)]),
     "tpc_tracker_set_timing": (c_int, [c_void_p, c_int]),
+    "tpc_tracker_inject": (c_int, [c_void_p, c_int]),
     "tpc_result_stats": (c_int, [c_void_p, P(tpc_call_stats)]),
     "tpc_find_links_noalloc": (c_int, [c_void_p, c_void_p, c_void_p, c_void_p, c_void_p, c_int64, c_void_p,
                                        c_void_p, c_void_p, c_void_p]),
@@ -236,6 +238,10 @@ def tpc_last_error_detail(tr):
     e, s, g = c_int(), c_int(), c_int()
     st = lib().tpc_last_error_detail(tr, ctypes.byref(e), ctypes.byref(s), ctypes.byref(g))
     return st, e.value, s.value, g.value
+
+
+def tpc_tracker_inject(tr, what):
+    _check(lib().tpc_tracker_inject(tr, int(what)), "tpc_tracker_inject")
 
 
 def tpc_tracker_set_timing(tr, enable=True):

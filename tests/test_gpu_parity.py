@@ -175,6 +175,19 @@ def test_full_central_event():
     tr.close()
 
 
+def test_full_central_event_sweep_constructor():
+    """Same workload with the sector-sweep constructor: identical to the oracle."""
+    ev = eventgen.config_event(2)
+    tr = Tracker.for_geometry(ev.geometry)
+    tr.set_tuning(dict(construct_mode=1))
+    _, out, _ = run_gpu(ev, tracker=tr, debug=False)
+    ref = run_oracle(ev, key="c2")
+    c = compare_tracks(ev, out, ref)
+    assert c["concordance"] >= CONCORDANCE_MIN and c["n_exact"] == c["n_matched"]
+    assert c["par_rel_max"].max() <= PAR_REL
+    tr.close()
+
+
 def test_single_sector_config0(ev0):
     tr, out, dbg = run_gpu(ev0)
     ref = run_oracle(ev0, key="c0")
@@ -236,7 +249,8 @@ def test_noisy_sector():
 @pytest.mark.parametrize("tuning", [
     dict(bin_occupancy=0.5), dict(bin_occupancy=16.0), dict(stage_rows=0),
     dict(neighbours_block=64, construct_block=64), dict(construct_block=96, construct_ctas_per_sm=1),
-    dict(bin_occupancy=2.0, neighbours_block=128, construct_ctas_per_sm=0)])
+    dict(bin_occupancy=2.0, neighbours_block=128, construct_ctas_per_sm=0), dict(construct_mode=1),
+    dict(construct_mode=1, bin_occupancy=4.0)])
 def test_tuning_does_not_change_results(tuning):
     """Grid bin size, block shapes and staging only change speed (the autotuner relies on it)."""
     ev = _small36()
@@ -329,3 +343,50 @@ def test_budget_is_enforced(ev1):
         tr.track(y, z, row, ev1.counts)
     assert e.value.status == 3
     tr.close()
+
+
+def test_expired_device_wait_is_reported():
+    """A bounded device wait that runs out (a staging wait for bytes nobody sends, injected from the
+    host) returns TPC_ERR_TIMEOUT; the context stays usable and the next call is correct."""
+    ev = _small36()
+    tr, ref, _ = run_gpu(ev, debug=False)
+    from paper_1712_09407_gb300.tracker import tpc_tracker_inject
+    tpc_tracker_inject(tr.handle, 1)
+    y, z, row = to_device(ev)
+    res = tr.track(y, z, row, ev.counts)
+    with pytest.raises(TrackerError) as e:
+        res.sync()
+    assert e.value.status == 4 and "neighbours" in str(e.value)
+    res.release()
+    tpc_tracker_inject(tr.handle, 0)
+    _, out, _ = run_gpu(ev, tracker=tr, debug=False)
+    for k in ref:
+        assert np.array_equal(ref[k], out[k]), k
+    tr.close()
+
+
+def test_tracklet_pool_overflow_is_reported():
+    """More start hits than the tracklet pool holds: TPC_ERR_CAPACITY with the stage, no crash."""
+    ev = _small36()
+    tr = Tracker.for_geometry(ev.geometry)
+    tr.set_tuning(dict(tracklet_capacity=100))
+    y, z, row = to_device(ev)
+    res = tr.track(y, z, row, ev.counts)
+    with pytest.raises(TrackerError) as e:
+        res.sync()
+    assert e.value.status == 2 and "evolution" in str(e.value)
+    res.release()
+    tr.close()
+
+
+def test_result_outlives_its_tracker():
+    """A result released after its tracker was destroyed is safe (the last release frees the rest)."""
+    ev = _small36()
+    tr = Tracker.for_geometry(ev.geometry)
+    y, z, row = to_device(ev)
+    res = tr.track(y, z, row, ev.counts)
+    m, _ = res.sync()
+    out = res.to_numpy()
+    tr.close()                                   # destroys the tracker while the result is held
+    assert len(out["first"]) == m > 0
+    res.release()
