@@ -22,11 +22,13 @@
 
 #ifdef ORC_F32
 typedef float real;
+#define FMA fmaf
 #define SQRT sqrtf
 #define FABS fabsf
 #define SFX(name) name##_f32
 #else
 typedef double real;
+#define FMA fma
 #define SQRT sqrt
 #define FABS fabs
 #define SFX(name) name##_f64
@@ -48,17 +50,17 @@ static float asin_ratio(float u)
     }
     float t = v * v;
     float s = 0.007312526f;                 /* 88179/12058624 */
-    s = s * t + 0.00839033537f;             /* 46189/5505024 */
-    s = s * t + 0.00976160914f;             /* 12155/1245184 */
-    s = s * t + 0.0115518011f;              /* 6435/557056 */
-    s = s * t + 0.0139648439f;              /* 143/10240 */
-    s = s * t + 0.0173527636f;              /* 231/13312 */
-    s = s * t + 0.0223721582f;              /* 63/2816 */
-    s = s * t + 0.030381944f;               /* 35/1152 */
-    s = s * t + 0.0446428582f;              /* 5/112 */
-    s = s * t + 0.075000003f;               /* 3/40 */
-    s = s * t + 0.166666672f;               /* 1/6 */
-    s = s * t + 1.0f;
+    s = fmaf(s, t, 0.00839033537f);         /* 46189/5505024 */
+    s = fmaf(s, t, 0.00976160914f);         /* 12155/1245184 */
+    s = fmaf(s, t, 0.0115518011f);          /* 6435/557056 */
+    s = fmaf(s, t, 0.0139648439f);          /* 143/10240 */
+    s = fmaf(s, t, 0.0173527636f);          /* 231/13312 */
+    s = fmaf(s, t, 0.0223721582f);          /* 63/2816 */
+    s = fmaf(s, t, 0.030381944f);           /* 35/1152 */
+    s = fmaf(s, t, 0.0446428582f);          /* 5/112 */
+    s = fmaf(s, t, 0.075000003f);           /* 3/40 */
+    s = fmaf(s, t, 0.166666672f);           /* 1/6 */
+    s = fmaf(s, t, 1.0f);
     if (m == 1.0f) return s;
     return ((m * v) * s) / u;
 }
@@ -237,49 +239,48 @@ static int propagate(KS *s, real x0, real x1, real kB, real smax)
     real dx = x1 - x0;
     real cur = kB * s->p[4];
     real s0 = s->p[2];
-    real s1 = s0 + cur * dx;
+    real s1 = FMA(cur, dx, s0);
     if (!(FABS(s1) < smax)) return 0;
-    real c0 = SQRT((real)1 - s0 * s0);
-    real c1 = SQRT((real)1 - s1 * s1);
+    real c0 = SQRT(FMA(-s0, s0, (real)1));
+    real c1 = SQRT(FMA(-s1, s1, (real)1));
     real A = s0 + s1;
     real B = c0 + c1;
     real tq = A / B;                          /* slope of the chord */
     real dy = dx * tq;
-    real L = SQRT(dx * dx + dy * dy);         /* chord, signed like dx */
+    real L = SQRT(FMA(dx, dx, dy * dy));      /* chord, signed like dx */
     if (dx < 0) L = -L;
     real u = (cur * L) * (real)0.5;           /* sin of half the turning angle */
     real ratio = asin_ratio(u);
     real dS = L * ratio;                      /* arc length = 2 asin(C L / 2) / C */
     real tl = s->p[3];
-    real dz = tl * dS;
 
     real F[5][5];
     memset(F, 0, sizeof F);
     for (int i = 0; i < 5; i++) F[i][i] = 1;
     real BB = B * B;
-    F[0][2] = dx * ((real)2 * B + A * (s0 / c0 + s1 / c1)) / BB;     /* d y1 / d sinphi0 */
-    F[0][4] = dx * (kB * dx) * (B + A * (s1 / c1)) / BB;             /* d y1 / d q/pT */
+    F[0][2] = dx * FMA(A, s0 / c0 + s1 / c1, (real)2 * B) / BB;       /* d y1 / d sinphi0 */
+    F[0][4] = dx * (kB * dx) * FMA(A, s1 / c1, B) / BB;               /* d y1 / d q/pT */
     F[2][4] = kB * dx;                                               /* d sinphi1 / d q/pT */
-    real g = (L != 0) ? ((real)1 / SQRT((real)1 - u * u)) * (dy / L) : (real)0; /* dS/dL * dL/ddy */
+    real g = (L != 0) ? ((real)1 / SQRT(FMA(-u, u, (real)1))) * (dy / L) : (real)0; /* dS/dL * dL/ddy */
     F[1][2] = tl * (g * F[0][2]);                                    /* d z1 / d sinphi0 */
     F[1][3] = dS;                                                    /* d z1 / d tanl */
-    F[1][4] = tl * (g * F[0][4] + (((cur * L) * (L * L)) / (real)12) * kB); /* d z1 / d q/pT */
+    F[1][4] = tl * FMA(g, F[0][4], (((cur * L) * (L * L)) / (real)12) * kB); /* d z1 / d q/pT */
 
     s->p[0] = s->p[0] + dy;
-    s->p[1] = s->p[1] + dz;
+    s->p[1] = FMA(tl, dS, s->p[1]);           /* z += tan(lambda) * arc length */
     s->p[2] = s1;
 
     real FC[5][5], N[5][5];
     for (int i = 0; i < 5; i++)
         for (int j = 0; j < 5; j++) {
             real a = 0;
-            for (int k = 0; k < 5; k++) a = a + F[i][k] * s->C[k][j];
+            for (int k = 0; k < 5; k++) a = FMA(F[i][k], s->C[k][j], a);
             FC[i][j] = a;
         }
     for (int i = 0; i < 5; i++)
         for (int j = 0; j < 5; j++) {
             real a = 0;
-            for (int k = 0; k < 5; k++) a = a + FC[i][k] * F[j][k];
+            for (int k = 0; k < 5; k++) a = FMA(FC[i][k], F[j][k], a);
             N[i][j] = a;
         }
     for (int i = 0; i < 5; i++)
@@ -295,7 +296,7 @@ typedef struct {
 static void residual_cov_inv(const KS *s, const K *k, Gain *g)
 {
     real S00 = s->C[0][0] + k->sy2, S01 = s->C[0][1], S10 = s->C[1][0], S11 = s->C[1][1] + k->sz2;
-    real det = S00 * S11 - S01 * S10;
+    real det = FMA(S00, S11, -S01 * S10);
     real idet = (real)1 / det;
     g->Si[0][0] = S11 * idet;
     g->Si[0][1] = -S01 * idet;
@@ -305,9 +306,9 @@ static void residual_cov_inv(const KS *s, const K *k, Gain *g)
 
 static real chi2_of(const Gain *g, real r0, real r1)
 {
-    real t0 = g->Si[0][0] * r0 + g->Si[0][1] * r1;
-    real t1 = g->Si[1][0] * r0 + g->Si[1][1] * r1;
-    return r0 * t0 + r1 * t1;
+    real t0 = FMA(g->Si[0][1], r1, g->Si[0][0] * r0);
+    real t1 = FMA(g->Si[1][1], r1, g->Si[1][0] * r0);
+    return FMA(r1, t1, r0 * t0);
 }
 
 /* Kalman update with measurement (my, mz): K = C H^T S^-1, p += K r, C -= K H C. */
@@ -318,16 +319,16 @@ static void kf_update(KS *s, const Gain *g, real my, real mz)
     for (int i = 0; i < 5; i++)
         for (int m = 0; m < 2; m++) {
             real a = 0;
-            for (int j = 0; j < 2; j++) a = a + s->C[i][j] * g->Si[j][m];
+            for (int j = 0; j < 2; j++) a = FMA(s->C[i][j], g->Si[j][m], a);
             Kg[i][m] = a;
         }
-    for (int i = 0; i < 5; i++) s->p[i] = s->p[i] + (Kg[i][0] * r0 + Kg[i][1] * r1);
+    for (int i = 0; i < 5; i++) s->p[i] = FMA(Kg[i][1], r1, FMA(Kg[i][0], r0, s->p[i]));
     real N[5][5];
     for (int i = 0; i < 5; i++)
         for (int j = 0; j < 5; j++) {
-            real a = 0;
-            for (int m = 0; m < 2; m++) a = a + Kg[i][m] * s->C[m][j];
-            N[i][j] = s->C[i][j] - a;
+            real a = s->C[i][j];
+            for (int m = 0; m < 2; m++) a = FMA(-Kg[i][m], s->C[m][j], a);
+            N[i][j] = a;
         }
     for (int i = 0; i < 5; i++)
         for (int j = 0; j <= i; j++) s->C[i][j] = s->C[j][i] = N[i][j];
@@ -400,7 +401,7 @@ static void sector_links(Sector *S, const K *k, const real *Y, const real *Zc, c
         real wyd = k->ty * dxd, wzd = k->tz * dxd;
         real w = dxd / (xu - xd);             /* weight of u in the interpolation at x_k */
         real om = (real)1 - w;
-        real gate = k->gate9 * (((real)1 + om * om) + w * w);
+        real gate = k->gate9 * FMA(w, w, FMA(om, om, (real)1));
         for (int64_t i = 0; i < rc->n; i++) {
             int64_t c = rc->off + i;
             real yc = Y[c], zc = Zc[c];
@@ -411,9 +412,9 @@ static void sector_links(Sector *S, const K *k, const real *Y, const real *Zc, c
             for (int a = 0; a < nu; a++)
                 for (int b = 0; b < nd; b++) {
                     int32_t u = buf_u[a], d = buf_d[b];
-                    real dy = (yc - Y[d]) - (Y[u] - Y[d]) * w;
-                    real dz = (zc - Zc[d]) - (Zc[u] - Zc[d]) * w;
-                    real sc = dy * dy * k->isy2 + dz * dz * k->isz2;
+                    real dy = FMA(-(Y[u] - Y[d]), w, yc - Y[d]);
+                    real dz = FMA(-(Zc[u] - Zc[d]), w, zc - Zc[d]);
+                    real sc = FMA(dz * dz, k->isz2, (dy * dy) * k->isy2);
                     int better = (bu < 0) || (sc < best) || (sc == best && (u < bu || (u == bu && d < bd)));
                     if (better) {
                         best = sc;
@@ -512,7 +513,7 @@ static void construct(Sector *S, const K *k, const real *Y, const real *Zc, cons
         real xr = k->X[r];
         pr = st;
         if (xr != xs && !propagate(&pr, xs, xr, k->kB, k->smax)) break;
-        if (FABS(pr.p[0]) > xr * k->th + k->margin) break;
+        if (FABS(pr.p[0]) > FMA(xr, k->th, k->margin)) break;
         residual_cov_inv(&pr, k, &g);
         int32_t b = search_row(S, k, Y, Zc, &pr, r, &g, &chi2, buf);
         if (b >= 0 && chi2 <= k->chi2max) {
@@ -540,7 +541,7 @@ static void construct(Sector *S, const K *k, const real *Y, const real *Zc, cons
         real xr = k->X[r];
         pr = st;
         if (xr != xs && !propagate(&pr, xs, xr, k->kB, k->smax)) break;
-        if (FABS(pr.p[0]) > xr * k->th + k->margin) break;
+        if (FABS(pr.p[0]) > FMA(xr, k->th, k->margin)) break;
         residual_cov_inv(&pr, k, &g);
         int32_t b = search_row(S, k, Y, Zc, &pr, r, &g, &chi2, buf);
         if (b >= 0 && chi2 <= k->chi2max) {

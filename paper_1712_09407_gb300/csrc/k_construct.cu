@@ -109,7 +109,7 @@ k_construct(const DevConst c, const Workspace w)
         bool stop = false;
         if (xr != xs && !propagate(pr, xr - xs, c)) {
             stop = true;
-        } else if (fabsf(pr.p0) > xr * c.th + c.margin) {
+        } else if (fabsf(pr.p0) > __fmaf_rn(xr, c.th, c.margin)) {
             stop = true;
         } else {
             visits++;

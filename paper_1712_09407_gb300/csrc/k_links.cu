@@ -206,9 +206,9 @@ __device__ __noinline__ void search_pairs_full(const DevConst &c, const RowView 
                     const float2 pd = D.yz[jd];
                     if (!(fabsf(pd.x - yc) <= wyd && fabsf(pd.y - zc) <= wzd)) continue;
                     // residual of c from the chord d -> u, evaluated at x_k (same order as the oracle)
-                    const float dy = (yc - pd.x) - (pu.x - pd.x) * w;
-                    const float dz = (zc - pd.y) - (pu.y - pd.y) * w;
-                    const float sc = dy * dy * c.isy2 + dz * dz * c.isz2;
+                    const float dy = __fmaf_rn(-(pu.x - pd.x), w, yc - pd.x);
+                    const float dz = __fmaf_rn(-(pu.y - pd.y), w, zc - pd.y);
+                    const float sc = __fmaf_rn(dz * dz, c.isz2, (dy * dy) * c.isy2);
                     if (bu >= 0 && sc > best) continue;
                     const int od = D.orig[jd];
                     if (bu < 0 || sc < best || ou < bou || (ou == bou && od < bod)) {
@@ -284,9 +284,9 @@ __device__ __forceinline__ void search_pairs(const DevConst &c, const RowView &U
             const int ou = U.orig[ju];
             for (int k = 0; k < nd; k++) {
                 // residual of c from the chord d -> u, evaluated at x_k (same order as the oracle)
-                const float dy = (yc - dly[k]) - (pu.x - dly[k]) * w;
-                const float dz = (zc - dlz[k]) - (pu.y - dlz[k]) * w;
-                const float sc = dy * dy * c.isy2 + dz * dz * c.isz2;
+                const float dy = __fmaf_rn(-(pu.x - dly[k]), w, yc - dly[k]);
+                const float dz = __fmaf_rn(-(pu.y - dlz[k]), w, zc - dlz[k]);
+                const float sc = __fmaf_rn(dz * dz, c.isz2, (dy * dy) * c.isy2);
                 if (bu >= 0 && sc > best) continue;
                 const int od = D.orig[dlj[k]];
                 if (bu < 0 || sc < best || ou < bou || (ou == bou && od < bod)) {
@@ -407,7 +407,7 @@ k_neighbours(const DevConst c, const Workspace w, int64_t R, int smem_bytes, int
         const float wyd = c.ty * dxd, wzd = c.tz * dxd;
         const float wgt = dxd / (xu - xd);
         const float om = 1.0f - wgt;
-        const float gate = c.gate9 * ((1.0f + om * om) + wgt * wgt);
+        const float gate = c.gate9 * __fmaf_rn(wgt, wgt, __fmaf_rn(om, om, 1.0f));
         for (int i = threadIdx.x; i < n; i += blockDim.x) {
             const float2 pc = w.yz[mk.z + i];
             int ou, od;

@@ -336,7 +336,7 @@ __global__ void __launch_bounds__(kSwThreads, 2) k_construct_sweep(const DevCons
                     bool stop = false;
                     if (xr != xs && !propagate(pr, xr - xs, c)) {
                         stop = true;
-                    } else if (fabsf(pr.p0) > xr * c.th + c.margin) {
+                    } else if (fabsf(pr.p0) > __fmaf_rn(xr, c.th, c.margin)) {
                         stop = true;
                     } else {
                         visits++;

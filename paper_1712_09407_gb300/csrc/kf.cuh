@@ -1,7 +1,7 @@
 // Kalman-filter pieces of the tracklet construction (Section 1, "Tracklet construction"), shared
 // by the two constructor kernels.  Expressions follow the same operation order as the CPU
-// oracle's float mode (the library is compiled without FMA contraction), so both evaluate
-// identical roundings.
+// oracle's float mode, with the same fused multiply-adds written out (the library is otherwise
+// compiled without FMA contraction), so both evaluate identical roundings.
 #pragma once
 #include "common.cuh"
 
@@ -26,86 +26,87 @@ __device__ __forceinline__ float asin_ratio(float u)
     }
     const float t = v * v;
     float s = 0.007312526f;
-    s = s * t + 0.00839033537f;
-    s = s * t + 0.00976160914f;
-    s = s * t + 0.0115518011f;
-    s = s * t + 0.0139648439f;
-    s = s * t + 0.0173527636f;
-    s = s * t + 0.0223721582f;
-    s = s * t + 0.030381944f;
-    s = s * t + 0.0446428582f;
-    s = s * t + 0.075000003f;
-    s = s * t + 0.166666672f;
-    s = s * t + 1.0f;
+    s = __fmaf_rn(s, t, 0.00839033537f);
+    s = __fmaf_rn(s, t, 0.00976160914f);
+    s = __fmaf_rn(s, t, 0.0115518011f);
+    s = __fmaf_rn(s, t, 0.0139648439f);
+    s = __fmaf_rn(s, t, 0.0173527636f);
+    s = __fmaf_rn(s, t, 0.0223721582f);
+    s = __fmaf_rn(s, t, 0.030381944f);
+    s = __fmaf_rn(s, t, 0.0446428582f);
+    s = __fmaf_rn(s, t, 0.075000003f);
+    s = __fmaf_rn(s, t, 0.166666672f);
+    s = __fmaf_rn(s, t, 1.0f);
     if (m == 1.0f) return s;
     return ((m * v) * s) / u;
 }
 
 // Exact helix transport by dx with covariance C <- F C F^T (F: Jacobian of the transport).
+// Fused multiply-adds are written out (__fmaf_rn) in the same places as in the oracle.
 __device__ __forceinline__ bool propagate(KF &s, float dx, const DevConst &c)
 {
     const float cur = c.kB * s.p4;
     const float s0 = s.p2;
-    const float s1 = s0 + cur * dx;
+    const float s1 = __fmaf_rn(cur, dx, s0);
     if (!(fabsf(s1) < c.smax)) return false;
-    const float c0 = sqrtf(1.0f - s0 * s0);
-    const float c1 = sqrtf(1.0f - s1 * s1);
+    const float c0 = sqrtf(__fmaf_rn(-s0, s0, 1.0f));
+    const float c1 = sqrtf(__fmaf_rn(-s1, s1, 1.0f));
     const float A = s0 + s1;
     const float B = c0 + c1;
     const float tq = A / B;
     const float dy = dx * tq;
-    float L = sqrtf(dx * dx + dy * dy);
+    float L = sqrtf(__fmaf_rn(dx, dx, dy * dy));
     if (dx < 0.0f) L = -L;
     const float u = (cur * L) * 0.5f;
     const float ratio = asin_ratio(u);
     const float dS = L * ratio;
     const float tl = s.p3;
-    const float dz = tl * dS;
     const float BB = B * B;
-    const float F02 = dx * (2.0f * B + A * (s0 / c0 + s1 / c1)) / BB;
-    const float F04 = dx * (c.kB * dx) * (B + A * (s1 / c1)) / BB;
+    const float s1c1 = s1 / c1;
+    const float F02 = dx * __fmaf_rn(A, s0 / c0 + s1c1, 2.0f * B) / BB;
+    const float F04 = dx * (c.kB * dx) * __fmaf_rn(A, s1c1, B) / BB;
     const float F24 = c.kB * dx;
-    const float g = (L != 0.0f) ? (1.0f / sqrtf(1.0f - u * u)) * (dy / L) : 0.0f;
+    const float g = (L != 0.0f) ? (1.0f / sqrtf(__fmaf_rn(-u, u, 1.0f))) * (dy / L) : 0.0f;
     const float F12 = tl * (g * F02);
     const float F13 = dS;
-    const float F14 = tl * (g * F04 + (((cur * L) * (L * L)) / 12.0f) * c.kB);
+    const float F14 = tl * __fmaf_rn(g, F04, (((cur * L) * (L * L)) / 12.0f) * c.kB);
 
     s.p0 = s.p0 + dy;
-    s.p1 = s.p1 + dz;
+    s.p1 = __fmaf_rn(tl, dS, s.p1);
     s.p2 = s1;
 
-    // FC = F C, row by row (k ascending, zero terms dropped)
+    // FC = F C, row by row (k ascending, zero terms dropped, unit terms exact)
     const float C00 = s.c00, C01 = s.c10, C02 = s.c20, C03 = s.c30, C04 = s.c40;
     const float C11 = s.c11, C12 = s.c21, C13 = s.c31, C14 = s.c41;
     const float C22 = s.c22, C23 = s.c32, C24 = s.c42;
     const float C33 = s.c33, C34 = s.c43, C44 = s.c44;
-    const float FC00 = (C00 + F02 * C02) + F04 * C04;
-    const float FC02 = (C02 + F02 * C22) + F04 * C24;
-    const float FC04 = (C04 + F02 * C24) + F04 * C44;
-    const float FC10 = ((C01 + F12 * C02) + F13 * C03) + F14 * C04;
-    const float FC11 = ((C11 + F12 * C12) + F13 * C13) + F14 * C14;
-    const float FC12 = ((C12 + F12 * C22) + F13 * C23) + F14 * C24;
-    const float FC13 = ((C13 + F12 * C23) + F13 * C33) + F14 * C34;
-    const float FC14 = ((C14 + F12 * C24) + F13 * C34) + F14 * C44;
-    const float FC20 = C02 + F24 * C04;
-    const float FC21 = C12 + F24 * C14;
-    const float FC22 = C22 + F24 * C24;
-    const float FC23 = C23 + F24 * C34;
-    const float FC24 = C24 + F24 * C44;
+    const float FC00 = __fmaf_rn(F04, C04, __fmaf_rn(F02, C02, C00));
+    const float FC02 = __fmaf_rn(F04, C24, __fmaf_rn(F02, C22, C02));
+    const float FC04 = __fmaf_rn(F04, C44, __fmaf_rn(F02, C24, C04));
+    const float FC10 = __fmaf_rn(F14, C04, __fmaf_rn(F13, C03, __fmaf_rn(F12, C02, C01)));
+    const float FC11 = __fmaf_rn(F14, C14, __fmaf_rn(F13, C13, __fmaf_rn(F12, C12, C11)));
+    const float FC12 = __fmaf_rn(F14, C24, __fmaf_rn(F13, C23, __fmaf_rn(F12, C22, C12)));
+    const float FC13 = __fmaf_rn(F14, C34, __fmaf_rn(F13, C33, __fmaf_rn(F12, C23, C13)));
+    const float FC14 = __fmaf_rn(F14, C44, __fmaf_rn(F13, C34, __fmaf_rn(F12, C24, C14)));
+    const float FC20 = __fmaf_rn(F24, C04, C02);
+    const float FC21 = __fmaf_rn(F24, C14, C12);
+    const float FC22 = __fmaf_rn(F24, C24, C22);
+    const float FC23 = __fmaf_rn(F24, C34, C23);
+    const float FC24 = __fmaf_rn(F24, C44, C24);
     // N = FC F^T, lower triangle (k ascending)
-    s.c00 = (FC00 + FC02 * F02) + FC04 * F04;
-    s.c10 = (FC10 + FC12 * F02) + FC14 * F04;
-    s.c11 = ((FC11 + FC12 * F12) + FC13 * F13) + FC14 * F14;
-    s.c20 = (FC20 + FC22 * F02) + FC24 * F04;
-    s.c21 = ((FC21 + FC22 * F12) + FC23 * F13) + FC24 * F14;
-    s.c22 = FC22 + FC24 * F24;
-    s.c30 = (C03 + C23 * F02) + C34 * F04;
-    s.c31 = ((C13 + C23 * F12) + C33 * F13) + C34 * F14;
-    s.c32 = C23 + C34 * F24;
+    s.c00 = __fmaf_rn(FC04, F04, __fmaf_rn(FC02, F02, FC00));
+    s.c10 = __fmaf_rn(FC14, F04, __fmaf_rn(FC12, F02, FC10));
+    s.c11 = __fmaf_rn(FC14, F14, __fmaf_rn(FC13, F13, __fmaf_rn(FC12, F12, FC11)));
+    s.c20 = __fmaf_rn(FC24, F04, __fmaf_rn(FC22, F02, FC20));
+    s.c21 = __fmaf_rn(FC24, F14, __fmaf_rn(FC23, F13, __fmaf_rn(FC22, F12, FC21)));
+    s.c22 = __fmaf_rn(FC24, F24, FC22);
+    s.c30 = __fmaf_rn(C34, F04, __fmaf_rn(C23, F02, C03));
+    s.c31 = __fmaf_rn(C34, F14, __fmaf_rn(C33, F13, __fmaf_rn(C23, F12, C13)));
+    s.c32 = __fmaf_rn(C34, F24, C23);
     // s.c33 unchanged
-    s.c40 = (C04 + C24 * F02) + C44 * F04;
-    s.c41 = ((C14 + C24 * F12) + C34 * F13) + C44 * F14;
-    s.c42 = C24 + C44 * F24;
+    s.c40 = __fmaf_rn(C44, F04, __fmaf_rn(C24, F02, C04));
+    s.c41 = __fmaf_rn(C44, F14, __fmaf_rn(C34, F13, __fmaf_rn(C24, F12, C14)));
+    s.c42 = __fmaf_rn(C44, F24, C24);
     // s.c43, s.c44 unchanged
     return true;
 }
@@ -117,7 +118,7 @@ struct Gain {
 __device__ __forceinline__ Gain residual_cov_inv(const KF &s, const DevConst &c)
 {
     const float S00 = s.c00 + c.sy2, S01 = s.c10, S10 = s.c10, S11 = s.c11 + c.sz2;
-    const float det = S00 * S11 - S01 * S10;
+    const float det = __fmaf_rn(S00, S11, -S01 * S10);
     const float idet = 1.0f / det;
     Gain g;
     g.s00 = S11 * idet;
@@ -129,43 +130,43 @@ __device__ __forceinline__ Gain residual_cov_inv(const KF &s, const DevConst &c)
 
 __device__ __forceinline__ float chi2_of(const Gain &g, float r0, float r1)
 {
-    const float t0 = g.s00 * r0 + g.s01 * r1;
-    const float t1 = g.s10 * r0 + g.s11 * r1;
-    return r0 * t0 + r1 * t1;
+    const float t0 = __fmaf_rn(g.s01, r1, g.s00 * r0);
+    const float t1 = __fmaf_rn(g.s11, r1, g.s10 * r0);
+    return __fmaf_rn(r1, t1, r0 * t0);
 }
 
 __device__ __forceinline__ void kf_update(KF &s, const Gain &g, float my, float mz)
 {
     const float r0 = my - s.p0, r1 = mz - s.p1;
     // K = C H^T S^-1
-    const float K00 = s.c00 * g.s00 + s.c10 * g.s10, K01 = s.c00 * g.s01 + s.c10 * g.s11;
-    const float K10 = s.c10 * g.s00 + s.c11 * g.s10, K11 = s.c10 * g.s01 + s.c11 * g.s11;
-    const float K20 = s.c20 * g.s00 + s.c21 * g.s10, K21 = s.c20 * g.s01 + s.c21 * g.s11;
-    const float K30 = s.c30 * g.s00 + s.c31 * g.s10, K31 = s.c30 * g.s01 + s.c31 * g.s11;
-    const float K40 = s.c40 * g.s00 + s.c41 * g.s10, K41 = s.c40 * g.s01 + s.c41 * g.s11;
-    s.p0 = s.p0 + (K00 * r0 + K01 * r1);
-    s.p1 = s.p1 + (K10 * r0 + K11 * r1);
-    s.p2 = s.p2 + (K20 * r0 + K21 * r1);
-    s.p3 = s.p3 + (K30 * r0 + K31 * r1);
-    s.p4 = s.p4 + (K40 * r0 + K41 * r1);
+    const float K00 = __fmaf_rn(s.c10, g.s10, s.c00 * g.s00), K01 = __fmaf_rn(s.c10, g.s11, s.c00 * g.s01);
+    const float K10 = __fmaf_rn(s.c11, g.s10, s.c10 * g.s00), K11 = __fmaf_rn(s.c11, g.s11, s.c10 * g.s01);
+    const float K20 = __fmaf_rn(s.c21, g.s10, s.c20 * g.s00), K21 = __fmaf_rn(s.c21, g.s11, s.c20 * g.s01);
+    const float K30 = __fmaf_rn(s.c31, g.s10, s.c30 * g.s00), K31 = __fmaf_rn(s.c31, g.s11, s.c30 * g.s01);
+    const float K40 = __fmaf_rn(s.c41, g.s10, s.c40 * g.s00), K41 = __fmaf_rn(s.c41, g.s11, s.c40 * g.s01);
+    s.p0 = __fmaf_rn(K01, r1, __fmaf_rn(K00, r0, s.p0));
+    s.p1 = __fmaf_rn(K11, r1, __fmaf_rn(K10, r0, s.p1));
+    s.p2 = __fmaf_rn(K21, r1, __fmaf_rn(K20, r0, s.p2));
+    s.p3 = __fmaf_rn(K31, r1, __fmaf_rn(K30, r0, s.p3));
+    s.p4 = __fmaf_rn(K41, r1, __fmaf_rn(K40, r0, s.p4));
     // C <- C - K H C (rows 0 and 1 of C are C(0, j) and C(1, j))
     const float A0 = s.c00, A1 = s.c10, A2 = s.c20, A3 = s.c30, A4 = s.c40;   // C(0, j)
     const float B0 = s.c10, B1 = s.c11, B2 = s.c21, B3 = s.c31, B4 = s.c41;   // C(1, j)
-    s.c00 = s.c00 - (K00 * A0 + K01 * B0);
-    s.c10 = s.c10 - (K10 * A0 + K11 * B0);
-    s.c11 = s.c11 - (K10 * A1 + K11 * B1);
-    s.c20 = s.c20 - (K20 * A0 + K21 * B0);
-    s.c21 = s.c21 - (K20 * A1 + K21 * B1);
-    s.c22 = s.c22 - (K20 * A2 + K21 * B2);
-    s.c30 = s.c30 - (K30 * A0 + K31 * B0);
-    s.c31 = s.c31 - (K30 * A1 + K31 * B1);
-    s.c32 = s.c32 - (K30 * A2 + K31 * B2);
-    s.c33 = s.c33 - (K30 * A3 + K31 * B3);
-    s.c40 = s.c40 - (K40 * A0 + K41 * B0);
-    s.c41 = s.c41 - (K40 * A1 + K41 * B1);
-    s.c42 = s.c42 - (K40 * A2 + K41 * B2);
-    s.c43 = s.c43 - (K40 * A3 + K41 * B3);
-    s.c44 = s.c44 - (K40 * A4 + K41 * B4);
+    s.c00 = __fmaf_rn(-K01, B0, __fmaf_rn(-K00, A0, s.c00));
+    s.c10 = __fmaf_rn(-K11, B0, __fmaf_rn(-K10, A0, s.c10));
+    s.c11 = __fmaf_rn(-K11, B1, __fmaf_rn(-K10, A1, s.c11));
+    s.c20 = __fmaf_rn(-K21, B0, __fmaf_rn(-K20, A0, s.c20));
+    s.c21 = __fmaf_rn(-K21, B1, __fmaf_rn(-K20, A1, s.c21));
+    s.c22 = __fmaf_rn(-K21, B2, __fmaf_rn(-K20, A2, s.c22));
+    s.c30 = __fmaf_rn(-K31, B0, __fmaf_rn(-K30, A0, s.c30));
+    s.c31 = __fmaf_rn(-K31, B1, __fmaf_rn(-K30, A1, s.c31));
+    s.c32 = __fmaf_rn(-K31, B2, __fmaf_rn(-K30, A2, s.c32));
+    s.c33 = __fmaf_rn(-K31, B3, __fmaf_rn(-K30, A3, s.c33));
+    s.c40 = __fmaf_rn(-K41, B0, __fmaf_rn(-K40, A0, s.c40));
+    s.c41 = __fmaf_rn(-K41, B1, __fmaf_rn(-K40, A1, s.c41));
+    s.c42 = __fmaf_rn(-K41, B2, __fmaf_rn(-K40, A2, s.c42));
+    s.c43 = __fmaf_rn(-K41, B3, __fmaf_rn(-K40, A3, s.c43));
+    s.c44 = __fmaf_rn(-K41, B4, __fmaf_rn(-K40, A4, s.c44));
 }
 
 __device__ __forceinline__ void set_seed_cov(KF &s, const DevConst &c)
