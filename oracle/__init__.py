@@ -70,7 +70,7 @@ class _Cfg(ctypes.Structure):
         ("edge_margin", ctypes.c_double), ("sin_max", ctypes.c_double),
         ("alpha", ctypes.c_double), ("beta", ctypes.c_double), ("min_clusters", ctypes.c_int),
         ("qpt_max", ctypes.c_double), ("bin_dy", ctypes.c_double), ("bin_dz", ctypes.c_double),
-        ("brute_force", ctypes.c_int), ("n_threads", ctypes.c_int),
+        ("brute_force", ctypes.c_int), ("n_threads", ctypes.c_int), ("global_tracking", ctypes.c_int),
     ]
 
 
@@ -78,7 +78,8 @@ INFO = ["n", "n_starts", "n_tracks", "n_track_hits", "n_rows", "visits", "candid
         "nb_candidates", "updates"]
 PTRS = ["up_raw", "dn_raw", "up", "dn", "starts", "tl_nhits", "tl_ndf", "tl_nup", "tl_hits",
         "tl_par", "tl_cov", "tl_x", "tl_chi2", "tl_w", "owner", "tl_nowned", "tl_accept",
-        "trk_tracklet", "trk_first", "trk_nhits", "trk_hits"]
+        "trk_tracklet", "trk_first", "trk_nhits", "trk_hits", "trk_par", "trk_cov", "trk_x", "trk_chi2",
+        "trk_ndf", "trk_sector", "trk_nglobal"]
 
 
 def lib():
@@ -98,6 +99,9 @@ def lib():
             L.orc_result_info.argtypes = [P, P]
             L.orc_result_ptrs.argtypes = [P, P]
             L.orc_result_free.argtypes = [P]
+            L.orc_rotate_f64.restype = ctypes.c_int
+            L.orc_rotate_f64.argtypes = [P, P, ctypes.c_double, ctypes.c_double, ctypes.c_double, ctypes.c_double,
+                                         ctypes.c_double, P]
             L.orc_seed_f64.restype = ctypes.c_int
             L.orc_seed_f64.argtypes = [P, P, P, ctypes.c_double, ctypes.c_double, P]
             L.orc_asin_ratio_f32.restype = ctypes.c_float
@@ -137,6 +141,7 @@ class Config:
     bin_dz: float = 4.0
     brute_force: bool = False
     n_threads: int = 0
+    global_tracking: bool = False
 
     def _c(self):
         rx = np.ascontiguousarray(self.row_x, dtype=np.float64)
@@ -149,6 +154,7 @@ class Config:
         for f in ("n_sectors", "min_chain", "max_miss", "min_clusters", "n_threads"):
             setattr(c, f, int(getattr(self, f)))
         c.brute_force = int(bool(self.brute_force))
+        c.global_tracking = int(bool(self.global_tracking))
         for i in range(5):
             c.seed_cov[i] = float(self.seed_cov[i])
         return c, rx
@@ -185,6 +191,13 @@ class Result:
     trk_first: np.ndarray
     trk_nhits: np.ndarray
     trk_hits: np.ndarray
+    trk_par: np.ndarray          # [M, 5] reported parameters (frame: trk_sector)
+    trk_cov: np.ndarray          # [M, 15]
+    trk_x: np.ndarray
+    trk_chi2: np.ndarray
+    trk_ndf: np.ndarray
+    trk_sector: np.ndarray
+    trk_nglobal: np.ndarray      # clusters added by global tracking
 
     def track_hits(self, i: int) -> np.ndarray:
         f = self.trk_first[i]
@@ -238,6 +251,11 @@ def track_event(cfg: Config, y, z, row, counts, precision: int = 32) -> Result:
             trk_tracklet=arr("trk_tracklet", i32, M, np.int32),
             trk_first=arr("trk_first", i32, M, np.int32), trk_nhits=arr("trk_nhits", i32, M, np.int32),
             trk_hits=arr("trk_hits", i32, H, np.int32),
+            trk_par=arr("trk_par", f64, M * 5, np.float64).reshape(M, 5),
+            trk_cov=arr("trk_cov", f64, M * 15, np.float64).reshape(M, 15),
+            trk_x=arr("trk_x", f64, M, np.float64), trk_chi2=arr("trk_chi2", f64, M, np.float64),
+            trk_ndf=arr("trk_ndf", i32, M, np.int32), trk_sector=arr("trk_sector", i32, M, np.int32),
+            trk_nglobal=arr("trk_nglobal", i32, M, np.int32),
         )
     finally:
         L.orc_result_free(h)
@@ -252,6 +270,17 @@ def propagate(state, cov15, x0, x1, bz=0.5, sin_max=0.99, precision: int = 64):
     fn = L.orc_propagate_f64 if precision == 64 else L.orc_propagate_f32
     ok = fn(s.ctypes.data, c.ctypes.data, float(x0), float(x1), float(bz), float(sin_max))
     return bool(ok), s, c
+
+
+def rotate(state, cov15, x, angle, bz=0.5, sin_max=0.99):
+    """Re-express a state at x in a frame rotated by `angle` (radians); returns (ok, state, cov, x')."""
+    L = lib()
+    s = np.array(state, dtype=np.float64)
+    c = np.array(cov15, dtype=np.float64)
+    xn = np.zeros(1)
+    ok = L.orc_rotate_f64(s.ctypes.data, c.ctypes.data, float(x), float(np.cos(angle)), float(np.sin(angle)),
+                          float(bz), float(sin_max), xn.ctypes.data)
+    return bool(ok), s, c, float(xn[0])
 
 
 def seed(x3, y3, z3, bz=0.5, sin_max=0.99):

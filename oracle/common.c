@@ -37,6 +37,7 @@ void orc_default_config(orc_config *c, const double *row_x, int n_rows, int n_se
     c->bin_dz = 4.0;
     c->brute_force = 0;
     c->n_threads = 0;
+    c->global_tracking = 0;
 }
 
 orc_result *orc_result_alloc(int64_t n, int n_rows)
@@ -76,6 +77,17 @@ void orc_result_alloc_tracklets(orc_result *r, int64_t t)
     r->trk_tracklet = (int32_t *)malloc(tt * sizeof(int32_t));
     r->trk_first = (int32_t *)malloc(tt * sizeof(int32_t));
     r->trk_nhits = (int32_t *)malloc(tt * sizeof(int32_t));
+    r->tl_opar = (double *)calloc(tt * 5, sizeof(double));
+    r->tl_ocov = (double *)calloc(tt * 15, sizeof(double));
+    r->tl_ox = (double *)calloc(tt, sizeof(double));
+    r->tl_orow = (int32_t *)calloc(tt, sizeof(int32_t));
+    r->trk_par = (double *)calloc(tt * 5, sizeof(double));
+    r->trk_cov = (double *)calloc(tt * 15, sizeof(double));
+    r->trk_x = (double *)calloc(tt, sizeof(double));
+    r->trk_chi2 = (double *)calloc(tt, sizeof(double));
+    r->trk_ndf = (int32_t *)calloc(tt, sizeof(int32_t));
+    r->trk_sector = (int32_t *)calloc(tt, sizeof(int32_t));
+    r->trk_nglobal = (int32_t *)calloc(tt, sizeof(int32_t));
 }
 
 void orc_result_info(const orc_result *r, int64_t *info)
@@ -111,6 +123,13 @@ void orc_result_ptrs(const orc_result *r, void **p)
     p[ORC_PTR_TRK_FIRST] = r->trk_first;
     p[ORC_PTR_TRK_NHITS] = r->trk_nhits;
     p[ORC_PTR_TRK_HITS] = r->trk_hits;
+    p[ORC_PTR_TRK_PAR] = r->trk_par;
+    p[ORC_PTR_TRK_COV] = r->trk_cov;
+    p[ORC_PTR_TRK_X] = r->trk_x;
+    p[ORC_PTR_TRK_CHI2] = r->trk_chi2;
+    p[ORC_PTR_TRK_NDF] = r->trk_ndf;
+    p[ORC_PTR_TRK_SECTOR] = r->trk_sector;
+    p[ORC_PTR_TRK_NGLOBAL] = r->trk_nglobal;
 }
 
 void orc_result_free(orc_result *r)
@@ -121,5 +140,8 @@ void orc_result_free(orc_result *r)
     free(r->tl_par); free(r->tl_cov); free(r->tl_x); free(r->tl_chi2); free(r->tl_w);
     free(r->tl_nowned); free(r->tl_accept);
     free(r->trk_tracklet); free(r->trk_first); free(r->trk_nhits); free(r->trk_hits);
+    free(r->tl_opar); free(r->tl_ocov); free(r->tl_ox); free(r->tl_orow);
+    free(r->trk_par); free(r->trk_cov); free(r->trk_x); free(r->trk_chi2);
+    free(r->trk_ndf); free(r->trk_sector); free(r->trk_nglobal);
     free(r);
 }

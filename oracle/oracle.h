@@ -51,6 +51,7 @@ typedef struct {
     double bin_dy, bin_dz;
     int brute_force;          /* 1: every search scans whole rows instead of grid bins */
     int n_threads;            /* OpenMP threads over sectors (<=0: runtime default) */
+    int global_tracking;      /* 1: prolong tracks across sector edges (Section 5) */
 } orc_config;
 
 /* Result of one event.  Indices of clusters are input ("original") indices. */
@@ -81,6 +82,9 @@ enum {
     ORC_PTR_TL_ACCEPT,                                                   /* uint8 [T] */
     ORC_PTR_TRK_TRACKLET, ORC_PTR_TRK_FIRST, ORC_PTR_TRK_NHITS,          /* int32 [M] */
     ORC_PTR_TRK_HITS,                                                    /* int32 [sum nhits], inner to outer */
+    ORC_PTR_TRK_PAR, ORC_PTR_TRK_COV, ORC_PTR_TRK_X, ORC_PTR_TRK_CHI2,    /* double [M*5], [M*15], [M], [M] */
+    ORC_PTR_TRK_NDF, ORC_PTR_TRK_SECTOR,                                 /* int32 [M]: frame sector of par */
+    ORC_PTR_TRK_NGLOBAL,                                                 /* int32 [M]: clusters added by global tracking */
     ORC_PTR_COUNT
 };
 
@@ -107,6 +111,10 @@ int orc_propagate_f64(double *state, double *cov15, double x0, double x1, double
 int orc_propagate_f32(double *state, double *cov15, double x0, double x1, double bz, double sin_max);
 /* asin(u)/u as the float mode evaluates it (series with half-angle reduction). */
 float orc_asin_ratio_f32(float u);
+/* Change of frame of a state at x by an azimuth rotation (cos, sin of the angle); returns 0
+ * if the direction does not point to increasing x in the new frame.  *x_new receives x'. */
+int orc_rotate_f64(double *state, double *cov15, double x, double cos_d, double sin_d, double bz, double sin_max,
+                   double *x_new);
 /* Seed state from three (x, y, z) points (first, middle, last of a chain). */
 int orc_seed_f64(const double *x3, const double *y3, const double *z3, double bz, double sin_max,
                  double *state);

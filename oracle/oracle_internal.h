@@ -17,6 +17,10 @@ struct orc_result {
     int32_t *owner, *tl_nowned;
     uint8_t *tl_accept;
     int32_t *trk_tracklet, *trk_first, *trk_nhits, *trk_hits;
+    double *tl_opar, *tl_ocov, *tl_ox;   /* outward-pass state at its last cluster (global tracking) */
+    int32_t *tl_orow;
+    double *trk_par, *trk_cov, *trk_x, *trk_chi2;
+    int32_t *trk_ndf, *trk_sector, *trk_nglobal;
 };
 
 orc_result *orc_result_alloc(int64_t n, int n_rows);

@@ -90,6 +90,9 @@ typedef struct {
     real kB;                      /* curvature per unit q/pT: -kappa * Bz */
     real bdy, bdz;
     int brute;
+    int global;
+    real c20, s20;                /* cos, sin of the 20 degree sector pitch */
+    int ns;
 } K;
 
 static void make_consts(K *k, const orc_config *c)
@@ -121,6 +124,10 @@ static void make_consts(K *k, const orc_config *c)
     k->bdy = (real)c->bin_dy;
     k->bdz = (real)c->bin_dz;
     k->brute = c->brute_force;
+    k->global = c->global_tracking && c->n_sectors == 36;
+    k->c20 = (real)cos(20.0 * 3.14159265358979323846 / 180.0);
+    k->s20 = (real)sin(20.0 * 3.14159265358979323846 / 180.0);
+    k->ns = c->n_sectors;
 }
 
 /* ----------------------------------------------------------------------------------------- */
@@ -189,13 +196,14 @@ static void bin_row(Row *rw, const real *Y, const real *Zc, real dy, real dz)
  * through the grid or, in brute-force mode, by scanning the whole row.  Returns
  * the count; *ncand receives the clusters looked at. */
 static int row_window(const Row *rw, const real *Y, const real *Zc, int brute, real yc, real zc,
-                      real wy, real wz, int32_t *out, int64_t *ncand)
+                      real wy, real wz, int32_t *out, int64_t *ncand, const uint8_t *used)
 {
     int cnt = 0;
     if (rw->n == 0) return 0;
     if (brute) {
         for (int64_t i = 0; i < rw->n; i++) {
             int64_t g = rw->off + i;
+            if (used && used[g]) continue;
             if (FABS(Y[g] - yc) <= wy && FABS(Zc[g] - zc) <= wz) out[cnt++] = (int32_t)g;
         }
         *ncand += rw->n;
@@ -210,6 +218,7 @@ static int row_window(const Row *rw, const real *Y, const real *Zc, int brute, r
         *ncand += b - a;
         for (int j = a; j < b; j++) {
             int32_t g = rw->sorted[j];
+            if (used && used[g]) continue;
             if (FABS(Y[g] - yc) <= wy && FABS(Zc[g] - zc) <= wz) out[cnt++] = g;
         }
     }
@@ -405,8 +414,8 @@ static void sector_links(Sector *S, const K *k, const real *Y, const real *Zc, c
         for (int64_t i = 0; i < rc->n; i++) {
             int64_t c = rc->off + i;
             real yc = Y[c], zc = Zc[c];
-            int nu = row_window(ru, Y, Zc, k->brute, yc, zc, wyu, wzu, buf_u, &S->cnt[ORC_INFO_NB_CANDIDATES]);
-            int nd = row_window(rd, Y, Zc, k->brute, yc, zc, wyd, wzd, buf_d, &S->cnt[ORC_INFO_NB_CANDIDATES]);
+            int nu = row_window(ru, Y, Zc, k->brute, yc, zc, wyu, wzu, buf_u, &S->cnt[ORC_INFO_NB_CANDIDATES], NULL);
+            int nd = row_window(rd, Y, Zc, k->brute, yc, zc, wyd, wzd, buf_d, &S->cnt[ORC_INFO_NB_CANDIDATES], NULL);
             int32_t bu = -1, bd = -1;
             real best = 0;
             for (int a = 0; a < nu; a++)
@@ -453,12 +462,12 @@ static void sector_links(Sector *S, const K *k, const real *Y, const real *Zc, c
 
 /* Best cluster of row r for state s: minimum chi2, ties to the lower input index. */
 static int32_t search_row(Sector *S, const K *k, const real *Y, const real *Zc, const KS *s, int r,
-                          const Gain *g, real *chi2_out, int32_t *buf)
+                          const Gain *g, real *chi2_out, int32_t *buf, const uint8_t *used)
 {
     const Row *rw = &S->rows[r];
     real wy = k->nsig * SQRT(s->C[0][0] + k->sy2);
     real wz = k->nsig * SQRT(s->C[1][1] + k->sz2);
-    int nc = row_window(rw, Y, Zc, k->brute, s->p[0], s->p[1], wy, wz, buf, &S->cnt[ORC_INFO_CANDIDATES]);
+    int nc = row_window(rw, Y, Zc, k->brute, s->p[0], s->p[1], wy, wz, buf, &S->cnt[ORC_INFO_CANDIDATES], used);
     S->cnt[ORC_INFO_IN_WINDOW] += nc;
     S->cnt[ORC_INFO_VISITS]++;
     int32_t best = -1;
@@ -515,7 +524,7 @@ static void construct(Sector *S, const K *k, const real *Y, const real *Zc, cons
         if (xr != xs && !propagate(&pr, xs, xr, k->kB, k->smax)) break;
         if (FABS(pr.p[0]) > FMA(xr, k->th, k->margin)) break;
         residual_cov_inv(&pr, k, &g);
-        int32_t b = search_row(S, k, Y, Zc, &pr, r, &g, &chi2, buf);
+        int32_t b = search_row(S, k, Y, Zc, &pr, r, &g, &chi2, buf, NULL);
         if (b >= 0 && chi2 <= k->chi2max) {
             kf_update(&pr, &g, Y[b], Zc[b]);
             S->cnt[ORC_INFO_UPDATES]++;
@@ -531,6 +540,15 @@ static void construct(Sector *S, const K *k, const real *Y, const real *Zc, cons
     res->tl_nup[t] = nup;
     if (rlast < 0) return;
 
+    /* the outward pass's state at its last cluster is the track's outer end (global tracking) */
+    {
+        int q = 0;
+        for (int i = 0; i < 5; i++) res->tl_opar[t * 5 + i] = (double)st.p[i];
+        for (int i = 0; i < 5; i++)
+            for (int j = 0; j <= i; j++) res->tl_ocov[t * 15 + q++] = (double)st.C[i][j];
+        res->tl_ox[t] = (double)xs;
+        res->tl_orow[t] = rlast;
+    }
     /* Inward pass from the outermost cluster, covariance reset to the seed's; its
      * clusters are the tracklet's, its last state is reported. */
     set_diag(&st, k->cov0);
@@ -543,7 +561,7 @@ static void construct(Sector *S, const K *k, const real *Y, const real *Zc, cons
         if (xr != xs && !propagate(&pr, xs, xr, k->kB, k->smax)) break;
         if (FABS(pr.p[0]) > FMA(xr, k->th, k->margin)) break;
         residual_cov_inv(&pr, k, &g);
-        int32_t b = search_row(S, k, Y, Zc, &pr, r, &g, &chi2, buf);
+        int32_t b = search_row(S, k, Y, Zc, &pr, r, &g, &chi2, buf, NULL);
         if (b >= 0 && chi2 <= k->chi2max) {
             chi2sum = chi2sum + chi2;
             kf_update(&pr, &g, Y[b], Zc[b]);
@@ -618,6 +636,108 @@ static void sector_select(Sector *S, const K *k, orc_result *res, int64_t t0, co
     S->tracks = (int32_t *)malloc(sizeof(int32_t) * (size_t)(na > 0 ? na : 1));
     for (int64_t i = 0; i < na; i++) S->tracks[i] = (int32_t)keys[2 * i + 1];
     free(keys);
+}
+
+/* Change of frame by an azimuth rotation (cos cd, sin sd): the state at x in the old frame is
+ * re-expressed at x' = x cd + y sd in the new frame (y' = -x sd + y cd, phi' = phi - angle), with
+ * the covariance transported by the Jacobian of the map to fixed x' (a change of y moves the
+ * point along x', which is taken back along the track).  Returns 0 if the direction does not
+ * point to increasing x' or |sin phi'| reaches smax. */
+static int rotate(KS *s, real x, real cd, real sd, real kB, real smax, real *x_new)
+{
+    real y = s->p[0], sp = s->p[2];
+    real cp = SQRT(FMA(-sp, sp, (real)1));
+    real xn = FMA(x, cd, y * sd);
+    real yn = FMA(y, cd, -(x * sd));
+    real spn = FMA(sp, cd, -(cp * sd));
+    if (!(FABS(spn) < smax)) return 0;
+    if (!(FMA(cp, cd, sp * sd) > 0)) return 0;          /* cos(phi') > 0 */
+    real cpn = SQRT(FMA(-spn, spn, (real)1));
+    real J[5][5];
+    memset(J, 0, sizeof J);
+    for (int i = 0; i < 5; i++) J[i][i] = 1;
+    J[0][0] = FMA(-sd, spn / cpn, cd);                 /* d y' / d y */
+    J[1][0] = -(sd * s->p[3]) / cpn;                   /* d z' / d y */
+    J[2][0] = -(kB * s->p[4]) * sd;                    /* d sinphi' / d y */
+    J[2][2] = cpn / cp;                                /* d sinphi' / d sinphi */
+    s->p[0] = yn;
+    s->p[2] = spn;
+    real JC[5][5], N[5][5];
+    for (int i = 0; i < 5; i++)
+        for (int j = 0; j < 5; j++) {
+            real a = 0;
+            for (int k = 0; k < 5; k++) a = FMA(J[i][k], s->C[k][j], a);
+            JC[i][j] = a;
+        }
+    for (int i = 0; i < 5; i++)
+        for (int j = 0; j < 5; j++) {
+            real a = 0;
+            for (int k = 0; k < 5; k++) a = FMA(JC[i][k], J[j][k], a);
+            N[i][j] = a;
+        }
+    for (int i = 0; i < 5; i++)
+        for (int j = 0; j <= i; j++) s->C[i][j] = s->C[j][i] = N[i][j];
+    *x_new = xn;
+    return 1;
+}
+
+/* Global tracking (Section 5): prolong a sector track from one of its ends into the neighbouring
+ * sector.  end: the state at x_end (row r_end) in sector s; dir = -1 inwards, +1 outwards.  The end
+ * counts as lying at the sector edge if the one-row extrapolation in its own sector leaves the
+ * row's width; then the state is rotated into the neighbour sector on that side (same z half) and
+ * the rows beyond x' are searched in direction dir with the construction's window, gate and stop
+ * rules, among the clusters of no accepted track (used[] == 0).  Returns the clusters found
+ * (hits_out, in search order); *fin receives the state at the last of them, *xfin its x, *sfin the
+ * neighbour sector. */
+static int prolong(Sector *S, const K *k, const real *Y, const real *Zc, int s, const KS *end, real x_end,
+                   int r_end, int dir, const uint8_t *used, int32_t *buf, int32_t *hits_out, real *chi2_out,
+                   KS *fin, real *xfin, int *sfin)
+{
+    int nr = k->nr;
+    *chi2_out = 0;
+    int rn = r_end + dir;
+    if (rn < 0 || rn >= nr) return 0;
+    KS pr = *end;
+    if (!propagate(&pr, x_end, k->X[rn], k->kB, k->smax)) return 0;
+    if (!(FABS(pr.p[0]) > k->X[rn] * k->th)) return 0;  /* still inside its sector */
+    int side = s / 18, az = s % 18;
+    int plus = pr.p[0] > 0;
+    int s2 = side * 18 + (plus ? (az + 1) % 18 : (az + 17) % 18);
+    KS st = *end;
+    real xs;
+    if (!rotate(&st, x_end, k->c20, plus ? k->s20 : -k->s20, k->kB, k->smax, &xs)) return 0;
+    int r = dir < 0 ? nr - 1 : 0;
+    if (dir < 0)
+        while (r >= 0 && !(k->X[r] < xs)) r--;
+    else
+        while (r < nr && !(k->X[r] > xs)) r++;
+    int n = 0, miss = 0;
+    real chi2sum = 0;
+    Gain g;
+    real chi2;
+    for (; r >= 0 && r < nr; r += dir) {
+        real xr = k->X[r];
+        pr = st;
+        if (!propagate(&pr, xs, xr, k->kB, k->smax)) break;
+        if (FABS(pr.p[0]) > FMA(xr, k->th, k->margin)) break;
+        residual_cov_inv(&pr, k, &g);
+        int32_t b = search_row(&S[s2], k, Y, Zc, &pr, r, &g, &chi2, buf, used);
+        if (b >= 0 && chi2 <= k->chi2max) {
+            chi2sum = chi2sum + chi2;
+            kf_update(&pr, &g, Y[b], Zc[b]);
+            st = pr;
+            xs = xr;
+            hits_out[n++] = b;
+            miss = 0;
+        } else if (++miss >= k->max_miss) {
+            break;
+        }
+    }
+    *chi2_out = chi2sum;
+    *fin = st;
+    *xfin = xs;
+    *sfin = s2;
+    return n;
 }
 
 orc_result *SFX(orc_track_event)(const orc_config *cfg, const double *y, const double *z,
@@ -698,29 +818,162 @@ orc_result *SFX(orc_track_event)(const orc_config *cfg, const double *y, const d
         free(chain);
     }
 
-    /* A7: concatenate sectors (input indices are grouped by sector, so this is the
-     * canonical order), hits from the innermost to the outermost row */
-    int64_t M = 0, H = 0;
-    for (int s = 0; s < ns; s++) {
-        M += S[s].ntracks;
-        for (int64_t i = 0; i < S[s].ntracks; i++) H += res->tl_nowned[S[s].tracks[i]];
+    /* tracks in canonical order (input indices are grouped by sector, so concatenating the
+     * sectors' sorted lists is the canonical order) */
+    int64_t M = 0;
+    for (int s = 0; s < ns; s++) M += S[s].ntracks;
+    int32_t *tk = (int32_t *)malloc(sizeof(int32_t) * (size_t)(M > 0 ? M : 1));
+    int32_t *tsec = (int32_t *)malloc(sizeof(int32_t) * (size_t)(M > 0 ? M : 1));
+    {
+        int64_t m = 0;
+        for (int s = 0; s < ns; s++)
+            for (int64_t i = 0; i < S[s].ntracks; i++) {
+                tk[m] = S[s].tracks[i];
+                tsec[m] = s;
+                m++;
+            }
+    }
+
+    /* Global tracking (Section 5): both ends of every track, then each contested cluster goes to
+     * the prolongation of the track with the higher weight (ties: the earlier start cluster, then
+     * the inward prolongation) */
+    int32_t *gh = NULL, *gn = NULL, *gown = NULL, *gsec = NULL;
+    real *gchi = NULL, *gx = NULL;
+    KS *gfin = NULL;
+    if (k.global && M > 0) {
+        uint8_t *used = (uint8_t *)calloc((size_t)(n > 0 ? n : 1), 1);
+        for (int64_t m = 0; m < M; m++) {
+            int32_t t = tk[m];
+            const int32_t *hh = res->tl_hits + (size_t)t * (size_t)nr;
+            for (int j = 0; j < res->tl_nhits[t]; j++)
+                if (res->owner[hh[j]] == t) used[hh[j]] = 1;
+        }
+        gh = (int32_t *)malloc(sizeof(int32_t) * (size_t)M * 2 * (size_t)nr);
+        gn = (int32_t *)calloc((size_t)M * 2, sizeof(int32_t));
+        gown = (int32_t *)calloc((size_t)M * 2, sizeof(int32_t));
+        gsec = (int32_t *)calloc((size_t)M * 2, sizeof(int32_t));
+        gchi = (real *)calloc((size_t)M * 2, sizeof(real));
+        gx = (real *)calloc((size_t)M * 2, sizeof(real));
+        gfin = (KS *)calloc((size_t)M * 2, sizeof(KS));
+#ifdef _OPENMP
+#pragma omp parallel num_threads(nth)
+#endif
+        {
+            int32_t *buf = (int32_t *)malloc(sizeof(int32_t) * (size_t)maxrow);
+#ifdef _OPENMP
+#pragma omp for schedule(dynamic, 64)
+#endif
+            for (int64_t m = 0; m < M; m++) {
+                int32_t t = tk[m];
+                for (int d = 0; d < 2; d++) {
+                    KS end;
+                    real xe;
+                    int re;
+                    if (d == 0) {           /* inner end: the reported state */
+                        for (int i = 0; i < 5; i++) end.p[i] = (real)res->tl_par[t * 5 + i];
+                        int q = 0;
+                        for (int i = 0; i < 5; i++)
+                            for (int j = 0; j <= i; j++, q++) end.C[i][j] = end.C[j][i] = (real)res->tl_cov[t * 15 + q];
+                        xe = (real)res->tl_x[t];
+                        re = row[res->tl_hits[(size_t)t * (size_t)nr + res->tl_nhits[t] - 1]];
+                    } else {                /* outer end: the outward pass's state */
+                        for (int i = 0; i < 5; i++) end.p[i] = (real)res->tl_opar[t * 5 + i];
+                        int q = 0;
+                        for (int i = 0; i < 5; i++)
+                            for (int j = 0; j <= i; j++, q++) end.C[i][j] = end.C[j][i] = (real)res->tl_ocov[t * 15 + q];
+                        xe = (real)res->tl_ox[t];
+                        re = res->tl_orow[t];
+                    }
+                    int64_t pi = m * 2 + d;
+                    gn[pi] = prolong(S, &k, Y, Zc, tsec[m], &end, xe, re, d == 0 ? -1 : 1, used, buf,
+                                     gh + (size_t)pi * (size_t)nr, &gchi[pi], &gfin[pi], &gx[pi], &gsec[pi]);
+                }
+            }
+            free(buf);
+        }
+        /* claims: each contested cluster goes to one prolongation */
+        int64_t *win = (int64_t *)malloc(sizeof(int64_t) * (size_t)(n > 0 ? n : 1));
+        for (int64_t i = 0; i < n; i++) win[i] = -1;
+        for (int64_t pi = 0; pi < M * 2; pi++)
+            for (int j = 0; j < gn[pi]; j++) {
+                int32_t c = gh[(size_t)pi * (size_t)nr + j];
+                int64_t o = win[c];
+                int better = o < 0;
+                if (!better) {
+                    int32_t ta = tk[pi / 2], tb = tk[o / 2];
+                    real wa = wv[ta], wb = wv[tb];
+                    if (wa > wb) better = 1;
+                    else if (wa == wb && res->starts[ta] < res->starts[tb]) better = 1;
+                    else if (wa == wb && res->starts[ta] == res->starts[tb] && (pi & 1) < (o & 1)) better = 1;
+                }
+                if (better) win[c] = pi;
+            }
+        /* keep only the clusters each prolongation owns, in search order */
+        for (int64_t pi = 0; pi < M * 2; pi++) {
+            int q = 0;
+            int32_t *hp = gh + (size_t)pi * (size_t)nr;
+            for (int j = 0; j < gn[pi]; j++)
+                if (win[hp[j]] == pi) hp[q++] = hp[j];
+            gown[pi] = q;
+        }
+        free(win);
+        free(used);
+    }
+
+    /* A7 output: hits from the innermost to the outermost cluster (inward prolongation, the
+     * sector's own clusters, outward prolongation) */
+    int64_t H = 0;
+    for (int64_t m = 0; m < M; m++) {
+        H += res->tl_nowned[tk[m]];
+        if (gown) H += gown[m * 2] + gown[m * 2 + 1];
     }
     res->n_tracks = M;
     res->n_track_hits = H;
     res->trk_hits = (int32_t *)malloc(sizeof(int32_t) * (size_t)(H > 0 ? H : 1));
-    int64_t m = 0, h = 0;
-    for (int s = 0; s < ns; s++) {
-        for (int64_t i = 0; i < S[s].ntracks; i++) {
-            int32_t t = S[s].tracks[i];
-            res->trk_tracklet[m] = t;
-            res->trk_first[m] = (int32_t)h;
-            res->trk_nhits[m] = res->tl_nowned[t];
-            const int32_t *hh = res->tl_hits + (size_t)t * (size_t)nr;
-            for (int j = res->tl_nhits[t] - 1; j >= 0; j--)
-                if (res->owner[hh[j]] == t) res->trk_hits[h++] = hh[j];
-            m++;
+    int64_t h = 0;
+    for (int64_t m = 0; m < M; m++) {
+        int32_t t = tk[m];
+        res->trk_tracklet[m] = t;
+        res->trk_first[m] = (int32_t)h;
+        int ng = 0;
+        if (gown)
+            for (int j = gown[m * 2] - 1; j >= 0; j--) res->trk_hits[h++] = gh[(size_t)(m * 2) * (size_t)nr + j];
+        const int32_t *hh = res->tl_hits + (size_t)t * (size_t)nr;
+        for (int j = res->tl_nhits[t] - 1; j >= 0; j--)
+            if (res->owner[hh[j]] == t) res->trk_hits[h++] = hh[j];
+        if (gown)
+            for (int j = 0; j < gown[m * 2 + 1]; j++) res->trk_hits[h++] = gh[(size_t)(m * 2 + 1) * (size_t)nr + j];
+        if (gown) ng = gown[m * 2] + gown[m * 2 + 1];
+        res->trk_nhits[m] = res->tl_nowned[t] + ng;
+        res->trk_nglobal[m] = ng;
+        /* parameters: the inward prolongation's last state if it fitted any cluster */
+        int inward = gn && gn[m * 2] > 0;
+        for (int i = 0; i < 5; i++) res->trk_par[m * 5 + i] = inward ? (double)gfin[m * 2].p[i] : res->tl_par[t * 5 + i];
+        int q = 0;
+        for (int i = 0; i < 5; i++)
+            for (int j = 0; j <= i; j++, q++)
+                res->trk_cov[m * 15 + q] = inward ? (double)gfin[m * 2].C[i][j] : res->tl_cov[t * 15 + q];
+        res->trk_x[m] = inward ? (double)gx[m * 2] : res->tl_x[t];
+        res->trk_sector[m] = inward ? gsec[m * 2] : tsec[m];
+        real chi = (real)res->tl_chi2[t];
+        int ndf = res->tl_ndf[t];
+        if (gn) {
+            chi = chi + gchi[m * 2];
+            chi = chi + gchi[m * 2 + 1];
+            ndf += 2 * (gn[m * 2] + gn[m * 2 + 1]);
         }
+        res->trk_chi2[m] = (double)chi;
+        res->trk_ndf[m] = ndf;
     }
+    free(tk);
+    free(tsec);
+    free(gh);
+    free(gn);
+    free(gown);
+    free(gsec);
+    free(gchi);
+    free(gx);
+    free(gfin);
     for (int s = 0; s < ns; s++)
         for (int i = 0; i < ORC_INFO_COUNT; i++) res->counters[i] += S[s].cnt[i];
 
@@ -764,6 +1017,24 @@ int SFX(orc_propagate)(double *state, double *cov15, double x0, double x1, doubl
 }
 
 #ifndef ORC_F32
+int orc_rotate_f64(double *state, double *cov15, double x, double cos_d, double sin_d, double bz, double sin_max,
+                   double *x_new)
+{
+    KS s;
+    for (int i = 0; i < 5; i++) s.p[i] = state[i];
+    int q = 0;
+    for (int i = 0; i < 5; i++)
+        for (int j = 0; j <= i; j++, q++) s.C[i][j] = s.C[j][i] = cov15[q];
+    double xn = 0;
+    int ok = rotate(&s, x, cos_d, sin_d, -ORC_KAPPA * bz, sin_max, &xn);
+    for (int i = 0; i < 5; i++) state[i] = s.p[i];
+    q = 0;
+    for (int i = 0; i < 5; i++)
+        for (int j = 0; j <= i; j++) cov15[q++] = s.C[i][j];
+    *x_new = xn;
+    return ok;
+}
+
 int orc_seed_f64(const double *x3, const double *y3, const double *z3, double bz, double sin_max,
                  double *state)
 {

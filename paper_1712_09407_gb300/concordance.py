@@ -96,7 +96,6 @@ def compare(ref, test, n_clusters, rows=None):
 
 def oracle_tracks(r):
     """Output dict of an oracle result (input indices, float64 parameters)."""
-    t = r.trk_tracklet
     return dict(first=r.trk_first.astype(np.int64), nhits=r.trk_nhits.astype(np.int64),
-                hits=r.trk_hits.astype(np.int64), par=r.tl_par[t], cov=r.tl_cov[t], x_ref=r.tl_x[t],
-                chi2=r.tl_chi2[t], ndf=r.tl_ndf[t])
+                hits=r.trk_hits.astype(np.int64), par=r.trk_par, cov=r.trk_cov, x_ref=r.trk_x,
+                chi2=r.trk_chi2, ndf=r.trk_ndf, sector=r.trk_sector)
