@@ -304,7 +304,7 @@ def run_ours(args):
     n_serial = min(args.steps, 40)
     starts = [torch.cuda.Event(enable_timing=True) for _ in range(n_serial)]
     ends = [torch.cuda.Event(enable_timing=True) for _ in range(n_serial)]
-    stage_ms = np.zeros(7)
+    stage_ms = np.zeros(8)
     stats_all = []
     results = []
     barrier()
@@ -365,7 +365,7 @@ def run_ours(args):
 
     if rank != 0:
         return 0
-    names = ["setup", "ingest", "neighbours", "evolution", "construction", "selection", "output"]
+    names = ["setup", "ingest", "neighbours", "evolution", "construction", "selection", "output", "global"]
     mean_stage = stage_ms / n_serial
     stages = {n: round(float(v), 4) for n, v in zip(names, mean_stage)}
     peak, peak_kind = measured_peaks()

@@ -58,7 +58,8 @@ enum {
     TPC_STAGE_EVOLUTION = 3,   /* A3 + A4 */
     TPC_STAGE_CONSTRUCTION = 4,/* A5 */
     TPC_STAGE_SELECTION = 5,   /* A6 */
-    TPC_STAGE_OUTPUT = 6       /* A7 */
+    TPC_STAGE_OUTPUT = 6,      /* A7 */
+    TPC_STAGE_GLOBAL = 7       /* global tracking (Section 5), between A6 and A7 */
 };
 
 /* Detector geometry (Section 1: two volumes of 18 trapezoidal sectors, 159 pad rows).
@@ -90,6 +91,8 @@ typedef struct {
     float alpha, beta;         /* cluster weight w = n * (alpha - (chi2/ndf) / beta) */
     int min_clusters;          /* minimum clusters of a track */
     float qpt_max;             /* low-momentum cut: |q/pT| <= qpt_max */
+    int global_tracking;       /* 1: prolong every track into the neighbouring sectors (Section 5); only
+                                  with 36 sectors, ignored otherwise; 0 by default */
 } tpc_params;
 
 /* Launch and grid choices.  None of them changes any result (every search
@@ -227,7 +230,7 @@ int tpc_last_error_detail(tpc_tracker *tr, int *event, int *sector, int *stage);
 
 /* Statistics of one call.  ms[] holds device milliseconds per stage, measured with
  * CUDA events on the call's stream when timing was enabled for the call (zeros
- * otherwise): ms[0] set-up copies and clears, ms[TPC_STAGE_INGEST .. TPC_STAGE_OUTPUT]
+ * otherwise): ms[0] set-up copies and clears, ms[TPC_STAGE_INGEST .. TPC_STAGE_GLOBAL]
  * the stages.  The counts are the work units the roofline figures are based on. */
 typedef struct {
     float ms[8];
@@ -238,6 +241,7 @@ typedef struct {
     int64_t candidates;            /* A5 clusters read inside the searched grid cells */
     int64_t tracks;                /* output tracks */
     int64_t hits;                  /* output clusters */
+    int64_t global_found;          /* clusters found by the global-tracking prolongations (before claims) */
 } tpc_call_stats;
 
 /* Host-side fault injection for failure tests; no GPU fault is involved.  what = 0: off;

@@ -90,7 +90,7 @@ struct tpc_result {
     int64_t n_clusters = 0;
     int launches = 0;
     bool timed = false;
-    cudaEvent_t stage_ev[8] = {};
+    cudaEvent_t stage_ev[9] = {};
 };
 
 bool tpc::tracker_info(const tpc_tracker *tr, TrackerInfo *out)
@@ -147,6 +147,7 @@ extern "C" void tpc_params_default(tpc_params *p)
     p->beta = 1.0f;
     p->min_clusters = 30;       // Section 5
     p->qpt_max = 20.0f;
+    p->global_tracking = 0;
 }
 
 extern "C" void tpc_tuning_default(tpc_tuning *t)
@@ -206,6 +207,9 @@ static void fill_const(tpc_tracker *tr, float bz)
     c.max_miss = p.max_miss;
     c.min_chain = p.min_chain;
     c.min_clusters = p.min_clusters;
+    c.global = (p.global_tracking && tr->n_sectors == 36) ? 1 : 0;
+    c.c20 = (float)std::cos(20.0 * 3.14159265358979323846 / 180.0);
+    c.s20 = (float)std::sin(20.0 * 3.14159265358979323846 / 180.0);
 }
 
 extern "C" int tpc_tracker_create(const tpc_geometry *g, float bz, const tpc_params *params, size_t budget,
@@ -309,6 +313,30 @@ static size_t carve(tpc_tracker *tr, const WsSizes &s, Alloc &a)
     w.tl_key = a.take<unsigned long long>(s.T);
     w.tl_nowned = a.take<int32_t>(s.T);
     w.tl_inner = a.take<int32_t>(s.T);
+    if (tr->dc.global) {
+        w.tl_opar = a.take<float>(5 * s.T);
+        w.tl_ocov = a.take<float>(15 * s.T);
+        w.tl_ox = a.take<float>(s.T);
+        w.used = a.take<uint8_t>(s.P);
+        w.gkey = a.take<unsigned long long>(s.P);
+        w.gpool = a.take<int32_t>(s.P);
+        w.gpool_cap = s.P;
+        w.g_off = a.take<int32_t>(2 * s.T);
+        w.g_n = a.take<int32_t>(2 * s.T);
+        w.g_own = a.take<int32_t>(2 * s.T);
+        w.g_chi = a.take<float>(2 * s.T);
+        w.g_list = a.take<int32_t>(2 * s.T);
+        w.g_par = a.take<float>(5 * s.T);
+        w.g_cov = a.take<float>(15 * s.T);
+        w.g_x = a.take<float>(s.T);
+        w.g_sec = a.take<int32_t>(s.T);
+    } else {
+        w.tl_opar = w.tl_ocov = w.tl_ox = w.g_chi = w.g_par = w.g_cov = w.g_x = nullptr;
+        w.used = nullptr;
+        w.gkey = nullptr;
+        w.gpool = w.g_off = w.g_n = w.g_own = w.g_list = w.g_sec = nullptr;
+        w.gpool_cap = 0;
+    }
     w.bits = a.take<uint32_t>(s.W);
     w.word_off = a.take<int32_t>(s.W);
     w.rank_trk = a.take<int32_t>(s.T);
@@ -416,7 +444,7 @@ static int run(tpc_tracker *tr, const float *y, const float *z, const uint8_t *r
         tr->free_results.pop_back();
         cudaEvent_t keep_done = res->done;
         int32_t *keep_counts = res->h_counts;
-        cudaEvent_t keep_ev[8];
+        cudaEvent_t keep_ev[9];
         memcpy(keep_ev, res->stage_ev, sizeof keep_ev);
         *res = tpc_result();
         res->done = keep_done;
@@ -561,6 +589,8 @@ static int run(tpc_tracker *tr, const float *y, const float *z, const uint8_t *r
     mark(5);
     launches += launch_select(tr->dc, w, n_total, lc, st);
     mark(6);
+    if (tr->dc.global) launches += launch_global(tr->dc, w, s_off, lc, st);
+    mark(8);
     launches += launch_output(tr->dc, w, res->out, n_total, lc, st);
     mark(7);
     TPC_CUDA(cudaGetLastError());
@@ -797,8 +827,12 @@ extern "C" int tpc_result_stats(tpc_result *r, tpc_call_stats *st)
     if (!r || !st) return TPC_ERR_INVALID_ARG;
     TPC_CUDA(cudaEventSynchronize(r->done));
     memset(st, 0, sizeof *st);
-    if (r->timed)
-        for (int i = 0; i < 7; i++) TPC_CUDA(cudaEventElapsedTime(&st->ms[i], r->stage_ev[i], r->stage_ev[i + 1]));
+    if (r->timed) {
+        // events: 0 start, 1..6 after set-up .. selection, 8 after global tracking, 7 after output
+        for (int i = 0; i < 6; i++) TPC_CUDA(cudaEventElapsedTime(&st->ms[i], r->stage_ev[i], r->stage_ev[i + 1]));
+        TPC_CUDA(cudaEventElapsedTime(&st->ms[TPC_STAGE_GLOBAL], r->stage_ev[6], r->stage_ev[8]));
+        TPC_CUDA(cudaEventElapsedTime(&st->ms[TPC_STAGE_OUTPUT], r->stage_ev[8], r->stage_ev[7]));
+    }
     st->kernel_launches = r->launches;
     st->clusters = r->n_clusters;
     st->tracklets = r->h_counts[CNT_STARTS];
@@ -806,6 +840,7 @@ extern "C" int tpc_result_stats(tpc_result *r, tpc_call_stats *st)
     st->candidates = r->h_counts[CNT_CANDS];
     st->tracks = r->h_counts[CNT_TRACKS];
     st->hits = r->h_counts[CNT_HITS];
+    st->global_found = r->h_counts[CNT_GPOOL];
     return TPC_OK;
 }
 

@@ -27,7 +27,9 @@ enum {
     CNT_VISITS = 4,     // A5 row visits (statistics)
     CNT_CANDS = 5,      // A5 clusters read inside the enumerated grid cells (statistics)
     CNT_SW_CHUNKS = 6,  // chunks of the sector-sweep constructor
-    CNT_COUNT = 8
+    CNT_GPOOL = 7,      // global tracking: clusters stored in the prolongation pool
+    CNT_GLIST = 8,      // global tracking: prolongations that found clusters
+    CNT_COUNT = 12
 };
 
 // Constants of one tracker, passed by value to every kernel (kernel parameter space).
@@ -53,6 +55,8 @@ struct DevConst {
     int min_chain;
     int min_clusters;
     int inject;         // host-side test hook (0 = off): 1 makes one staging wait of the neighbours finder expire
+    int global;         // global tracking on (Section 5)
+    float c20, s20;     // cos, sin of the 20 degree sector pitch
 };
 
 // Per row unit metadata (host-computed): input offset, count, sorted offset, cell offset.
@@ -83,6 +87,17 @@ struct Workspace {
     unsigned long long *tl_key;
     int32_t *tl_nowned;
     int32_t *tl_inner;     // input index of the innermost owned cluster, -1 if rejected
+    // global tracking (Section 5)
+    float *tl_opar, *tl_ocov, *tl_ox;   // outward pass's state at its last cluster [5|15|1][tcap]
+    uint8_t *used;         // [slots] cluster of an accepted track
+    unsigned long long *gkey;   // [slots] prolongation claims
+    int32_t *gpool;        // [gpool_cap] clusters found by prolongations
+    int64_t gpool_cap;
+    int32_t *g_off, *g_n, *g_own;       // [2 * tcap] per (tracklet, end)
+    float *g_chi;          // [2 * tcap]
+    float *g_par, *g_cov, *g_x;         // inward prolongation's last state [5|15|1][tcap]
+    int32_t *g_sec;        // [tcap] sector (within the event) of that state
+    int32_t *g_list;       // [2 * tcap] prolongations that found clusters
     // output ordering
     uint32_t *bits;        // bitmap over input indices of innermost clusters
     int32_t *word_off;     // exclusive prefix of popcounts
@@ -134,6 +149,16 @@ __device__ __forceinline__ uint32_t ordered_bits(float f)
 {
     uint32_t b = __float_as_uint(f);
     return (b & 0x80000000u) ? ~b : (b | 0x80000000u);
+}
+
+// Claim key of global-tracking prolongation (t, d) (d = 0 inward, 1 outward): the track's weight,
+// then the lower input index of its start cluster, then the inward end.
+__device__ __forceinline__ unsigned long long prolong_key(const Workspace &w, int t, int d)
+{
+    const uint32_t hi = ordered_bits(w.tl_w[t]);
+    const uint32_t o = (uint32_t)w.orig[w.starts[t].x];
+    const uint32_t lo = ((0x7fffffffu - o) << 1) | (uint32_t)(1 - d);
+    return ((unsigned long long)hi << 32) | lo;
 }
 
 // Grid cell along one axis; monotone non-decreasing in v.
@@ -191,6 +216,7 @@ int launch_construct_sweep(const DevConst &c, const Workspace &w, int n_sec, con
 int launch_select(const DevConst &c, const Workspace &w, int64_t n_input, const LaunchCfg &lc, cudaStream_t s);
 int launch_output(const DevConst &c, const Workspace &w, const OutBuffers &o, int64_t n_input,
                    const LaunchCfg &lc, cudaStream_t s);
+int launch_global(const DevConst &c, const Workspace &w, int64_t n_slots, const LaunchCfg &lc, cudaStream_t s);
 int neighbours_smem_limit();
 
 // Read-only view of a tracker's constants for entry points defined outside api.cu.

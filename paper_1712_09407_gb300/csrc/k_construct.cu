@@ -70,12 +70,14 @@ __global__ void __launch_bounds__(256) k_order_scatter(const DevConst c, const W
     }
 }
 
-// 128 threads and 6 resident CTAs per SM: 80 registers without spills (measured fastest)
+// 128 threads and 6 resident CTAs per SM: 80 registers without spills (measured fastest).
+// GLOBAL: also store the outward pass's final state (the outer end for global tracking); a
+// separate instance so that the plain tracker keeps its register allocation.
+template <bool GLOBAL>
 __global__ void __launch_bounds__(128, 6)
 k_construct(const DevConst c, const Workspace w)
 {
     const int T = n_tracklets(w);
-    const int tcap = (int)w.tcap;
     int phase = 0;            // 0: needs a tracklet, 1: outward pass, 2: inward pass
     int t = 0, sec = 0, r = 0, rlast = -1, miss = 0, n = 0, orig0 = 0;
     float xs = 0.0f, chi2sum = 0.0f;
@@ -144,6 +146,7 @@ k_construct(const DevConst c, const Workspace w)
                 if (rlast < 0) {
                     phase = 0;
                 } else {
+                    if (GLOBAL) write_outer(w, t, st, xs);   // outer end for global tracking
                     set_seed_cov(st, c);
                     r = rlast;
                     miss = 0;
@@ -175,7 +178,8 @@ int launch_construct(const DevConst &c, const Workspace &w, const LaunchCfg &lc,
     int per_sm = lc.construct_ctas_per_sm;
     if (per_sm <= 0) {
         int occ = 0;
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_construct, lc.construct_block, 0);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, c.global ? k_construct<true> : k_construct<false>,
+                                                      lc.construct_block, 0);
         per_sm = occ > 0 ? occ : 1;
     }
     cudaMemsetAsync(w.buckets, 0, kOrderBuckets * sizeof(int32_t), s);
@@ -183,7 +187,10 @@ int launch_construct(const DevConst &c, const Workspace &w, const LaunchCfg &lc,
     k_order_hist<<<og, 256, 0, s>>>(c, w);
     k_order_scan<<<1, kOrderBuckets, 0, s>>>(w);
     k_order_scatter<<<og, 256, 0, s>>>(c, w);
-    k_construct<<<lc.num_sms * per_sm, lc.construct_block, 0, s>>>(c, w);
+    if (c.global)
+        k_construct<true><<<lc.num_sms * per_sm, lc.construct_block, 0, s>>>(c, w);
+    else
+        k_construct<false><<<lc.num_sms * per_sm, lc.construct_block, 0, s>>>(c, w);
     return 4;
 }
 

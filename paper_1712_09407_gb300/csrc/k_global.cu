@@ -1,0 +1,245 @@
+// Global tracking (Section 5): every track is prolonged from both of its ends into the
+// neighbouring sector, and the clusters found there are merged into the track.
+//
+// An end counts as lying at a sector edge if its one-row extrapolation in its own sector
+// leaves the row's width.  Its state is then rotated into the neighbour sector on that side
+// (same z half), and the rows beyond it are searched in the same direction with the
+// construction's window, gate and stop rules, among the clusters that belong to no accepted
+// track.  Clusters found by several prolongations go to the track of the higher weight (then the
+// lower input index of its start cluster, then the inward prolongation), with one 64-bit
+// atomicMax per cluster as in the selection.  A track's inward prolongation, if it fitted any
+// cluster, gives the reported state.
+//
+// The prolongations of a call are few and mostly end at the edge test, so one thread takes one
+// (track, end) pair.  Pass 1 runs every prolongation without storing anything but its count,
+// chi2 and final state, and reserves its range of the pool; pass 2 runs again only the
+// prolongations that found clusters (same inputs, same arithmetic, same clusters) and stores and
+// claims them; pass 3 counts what each prolongation owns.  The track's output assembles the
+// owned clusters inner to outer.
+#include "kf.cuh"
+#include "../../include/tpcca.h"
+
+namespace tpc {
+
+constexpr int kGlobalBlock = 128;
+
+// Row whose radius is x (x is one of the row radii, which strictly increase).
+__device__ __forceinline__ int row_of_x(const DevConst &c, float x)
+{
+    int lo = 0, hi = c.nr - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi) >> 1;
+        if (c.row_x[mid] < x)
+            lo = mid + 1;
+        else
+            hi = mid;
+    }
+    return lo;
+}
+
+__device__ __forceinline__ void load_state(const float *P, const float *V, int tcap, int t, KF &s)
+{
+    s.p0 = P[0 * tcap + t]; s.p1 = P[1 * tcap + t]; s.p2 = P[2 * tcap + t]; s.p3 = P[3 * tcap + t];
+    s.p4 = P[4 * tcap + t];
+    s.c00 = V[0 * tcap + t]; s.c10 = V[1 * tcap + t]; s.c11 = V[2 * tcap + t]; s.c20 = V[3 * tcap + t];
+    s.c21 = V[4 * tcap + t]; s.c22 = V[5 * tcap + t]; s.c30 = V[6 * tcap + t]; s.c31 = V[7 * tcap + t];
+    s.c32 = V[8 * tcap + t]; s.c33 = V[9 * tcap + t]; s.c40 = V[10 * tcap + t]; s.c41 = V[11 * tcap + t];
+    s.c42 = V[12 * tcap + t]; s.c43 = V[13 * tcap + t]; s.c44 = V[14 * tcap + t];
+}
+
+__device__ __forceinline__ void store_state(float *P, float *V, int tcap, int t, const KF &s)
+{
+    P[0 * tcap + t] = s.p0; P[1 * tcap + t] = s.p1; P[2 * tcap + t] = s.p2; P[3 * tcap + t] = s.p3;
+    P[4 * tcap + t] = s.p4;
+    V[0 * tcap + t] = s.c00; V[1 * tcap + t] = s.c10; V[2 * tcap + t] = s.c11; V[3 * tcap + t] = s.c20;
+    V[4 * tcap + t] = s.c21; V[5 * tcap + t] = s.c22; V[6 * tcap + t] = s.c30; V[7 * tcap + t] = s.c31;
+    V[8 * tcap + t] = s.c32; V[9 * tcap + t] = s.c33; V[10 * tcap + t] = s.c40; V[11 * tcap + t] = s.c41;
+    V[12 * tcap + t] = s.c42; V[13 * tcap + t] = s.c43; V[14 * tcap + t] = s.c44;
+}
+
+// The end state of prolongation (t, d) with its x and row.
+__device__ __forceinline__ void end_state(const DevConst &c, const Workspace &w, int t, int d, KF &s, float &x,
+                                          int &r)
+{
+    const int tcap = (int)w.tcap;
+    if (d == 0) {          // inner end: the reported state, at the innermost fitted cluster
+        load_state(w.tl_par, w.tl_cov, tcap, t, s);
+        x = w.tl_x[t];
+    } else {               // outer end: the outward pass's state at its last cluster
+        load_state(w.tl_opar, w.tl_ocov, tcap, t, s);
+        x = w.tl_ox[t];
+    }
+    r = row_of_x(c, x);
+}
+
+// One prolongation from `end` (at x_end, row r_end, sector `sec` of the call) in direction dir.
+// Returns the clusters found; with STORE the first nmax of them are written to out[] (slots) and
+// claimed with key.
+template <bool STORE>
+__device__ int prolong(const DevConst &c, const Workspace &w, int sec, const KF &end, float x_end, int r_end,
+                       int dir, int32_t *out, int nmax, unsigned long long key, float &chi2_out, KF &fin,
+                       float &x_fin, int &s2_out)
+{
+    chi2_out = 0.0f;
+    const int rn = r_end + dir;
+    if (rn < 0 || rn >= c.nr) return 0;
+    KF pr = end;
+    if (!propagate(pr, c.row_x[rn] - x_end, c)) return 0;
+    if (!(fabsf(pr.p0) > c.row_x[rn] * c.th)) return 0;      // still inside its own sector
+    const int ev = sec / c.ns, s = sec % c.ns;
+    const int side = s / 18, az = s % 18;
+    const bool plus = pr.p0 > 0.0f;
+    const int s2 = side * 18 + (plus ? (az + 1) % 18 : (az + 17) % 18);
+    KF st = end;
+    float xs;
+    if (!rotate_state(st, x_end, c.c20, plus ? c.s20 : -c.s20, c, xs)) return 0;
+    int r;
+    if (dir < 0) {
+        r = c.nr - 1;
+        while (r >= 0 && !(c.row_x[r] < xs)) r--;
+    } else {
+        r = 0;
+        while (r < c.nr && !(c.row_x[r] > xs)) r++;
+    }
+    const int gsec = ev * c.ns + s2;
+    int n = 0, miss = 0, cands = 0;
+    float chi2sum = 0.0f;
+    for (; r >= 0 && r < c.nr; r += dir) {
+        const float xr = c.row_x[r];
+        KF p = st;
+        if (!propagate(p, xr - xs, c)) break;
+        if (fabsf(p.p0) > __fmaf_rn(xr, c.th, c.margin)) break;
+        const Gain g = residual_cov_inv(p, c);
+        const int4 rg = w.rgi[gsec * c.nr + r];
+        const float4 gr = w.grid[gsec * c.nr + r];
+        float chi2 = 0.0f;
+        const int bl = search_cells(c, w.yz + rg.x, w.orig + rg.x, w.cell + rg.y, gr, rg.z, rg.w, p, g, chi2, cands,
+                                    w.used + rg.x);
+        if (bl >= 0 && chi2 <= c.chi2max) {
+            const int b = rg.x + bl;
+            chi2sum = chi2sum + chi2;
+            const float2 q = w.yz[b];
+            kf_update(p, g, q.x, q.y);
+            st = p;
+            xs = xr;
+            if (STORE && n < nmax) {
+                out[n] = b;
+                atomicMax(&w.gkey[b], key);
+            }
+            n++;
+            miss = 0;
+        } else if (++miss >= c.max_miss) {
+            break;
+        }
+    }
+    chi2_out = chi2sum;
+    fin = st;
+    x_fin = xs;
+    s2_out = s2;
+    return n;
+}
+
+// Clusters owned by accepted tracks are closed to the prolongations.
+__global__ void __launch_bounds__(256) k_global_used(const DevConst c, const Workspace w)
+{
+    const int T = n_tracklets(w);
+    const int lane = threadIdx.x & 31;
+    const int nwarps = (gridDim.x * blockDim.x) >> 5;
+    for (int t = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; t < T; t += nwarps) {
+        if (w.tl_inner[t] < 0) continue;
+        const unsigned long long key = w.tl_key[t];
+        const int n = w.tl_n[t];
+        const int32_t *h = w.tl_hits + (int64_t)t * c.nr;
+        for (int i = lane; i < n; i += 32)
+            if (w.ckey[h[i]] == key) w.used[h[i]] = 1;
+    }
+}
+
+// Pass 1: every prolongation of every accepted track; counts, chi2, final inward state, pool range.
+__global__ void __launch_bounds__(kGlobalBlock) k_global_find(const DevConst c, const Workspace w)
+{
+    const int T = n_tracklets(w);
+    const int tcap = (int)w.tcap;
+    for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < 2 * T; p += gridDim.x * blockDim.x) {
+        const int t = p >> 1, d = p & 1;
+        int n = 0;
+        float chi = 0.0f;
+        int off = -1;
+        if (w.tl_inner[t] >= 0) {
+            KF end, fin;
+            float xe, xf;
+            int re, s2;
+            end_state(c, w, t, d, end, xe, re);
+            const int sec = w.starts[t].w >> 16;
+            n = prolong<false>(c, w, sec, end, xe, re, d == 0 ? -1 : 1, nullptr, 0, 0ull, chi, fin, xf, s2);
+            if (d == 0 && n > 0) {
+                store_state(w.g_par, w.g_cov, tcap, t, fin);
+                w.g_x[t] = xf;
+                w.g_sec[t] = s2;
+            }
+            if (n > 0) {
+                const int o = atomicAdd(&w.counters[CNT_GPOOL], n);
+                if ((int64_t)o + n > w.gpool_cap) {
+                    set_error(w.err, TPC_ERR_CAPACITY, sec * c.nr, c, TPC_STAGE_GLOBAL);
+                } else {
+                    off = o;
+                    w.g_list[atomicAdd(&w.counters[CNT_GLIST], 1)] = p;
+                }
+            }
+        }
+        w.g_n[p] = n;
+        w.g_chi[p] = chi;
+        w.g_off[p] = off;
+        w.g_own[p] = 0;
+    }
+}
+
+// Pass 2: the prolongations that found clusters store and claim them.
+__global__ void __launch_bounds__(kGlobalBlock) k_global_store(const DevConst c, const Workspace w)
+{
+    const int L = w.counters[CNT_GLIST];
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < L; i += gridDim.x * blockDim.x) {
+        const int p = w.g_list[i];
+        const int t = p >> 1, d = p & 1;
+        KF end, fin;
+        float xe, xf, chi;
+        int re, s2;
+        end_state(c, w, t, d, end, xe, re);
+        const int sec = w.starts[t].w >> 16;
+        // same inputs and arithmetic as pass 1, so the same g_n[p] clusters (nmax only bounds the writes)
+        prolong<true>(c, w, sec, end, xe, re, d == 0 ? -1 : 1, w.gpool + w.g_off[p], w.g_n[p], prolong_key(w, t, d),
+                      chi, fin, xf, s2);
+    }
+}
+
+// Pass 3: clusters each prolongation owns.
+__global__ void __launch_bounds__(256) k_global_own(const Workspace w)
+{
+    const int L = w.counters[CNT_GLIST];
+    const int lane = threadIdx.x & 31;
+    const int nwarps = (gridDim.x * blockDim.x) >> 5;
+    for (int i = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; i < L; i += nwarps) {
+        const int p = w.g_list[i];
+        const unsigned long long key = prolong_key(w, p >> 1, p & 1);
+        const int n = w.g_n[p];
+        const int32_t *h = w.gpool + w.g_off[p];
+        int own = 0;
+        for (int j = lane; j < n; j += 32) own += (w.gkey[h[j]] == key);
+        for (int o = 16; o > 0; o >>= 1) own += __shfl_xor_sync(kFull, own, o);
+        if (lane == 0) w.g_own[p] = own;
+    }
+}
+
+int launch_global(const DevConst &c, const Workspace &w, int64_t n_slots, const LaunchCfg &lc, cudaStream_t s)
+{
+    cudaMemsetAsync(w.used, 0, (size_t)n_slots, s);
+    cudaMemsetAsync(w.gkey, 0, (size_t)n_slots * sizeof(unsigned long long), s);
+    const int grid = lc.num_sms * 8;
+    k_global_used<<<grid, 256, 0, s>>>(c, w);
+    k_global_find<<<lc.num_sms * 8, kGlobalBlock, 0, s>>>(c, w);
+    k_global_store<<<lc.num_sms * 2, kGlobalBlock, 0, s>>>(c, w);
+    k_global_own<<<grid, 256, 0, s>>>(w);
+    return 4;
+}
+
+}  // namespace tpc

@@ -197,7 +197,7 @@ int launch_select(const DevConst &c, const Workspace &w, int64_t n_input, const 
 // ---------------------------------------------------------------------------------------------
 // A7
 // ---------------------------------------------------------------------------------------------
-__global__ void __launch_bounds__(256) k_rank(const Workspace w)
+__global__ void __launch_bounds__(256) k_rank(const DevConst c, const Workspace w)
 {
     const int T = n_tracklets(w);
     for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < T; t += gridDim.x * blockDim.x) {
@@ -206,8 +206,28 @@ __global__ void __launch_bounds__(256) k_rank(const Workspace w)
         const uint32_t word = w.bits[o >> 5];
         const int rank = w.word_off[o >> 5] + __popc(word & ((1u << (o & 31)) - 1u));
         w.rank_trk[rank] = t;
-        w.rank_first[rank] = w.tl_nowned[t];
+        w.rank_first[rank] = w.tl_nowned[t] + (c.global ? w.g_own[2 * t] + w.g_own[2 * t + 1] : 0);
     }
+}
+
+// Clusters of prolongation p that it owns (claim key equal to its own), written from pos on in
+// search order (reverse = false) or reversed; returns the position after them.
+__device__ __forceinline__ int write_prolongation(const Workspace &w, const OutBuffers &o, int p, int pos,
+                                                  bool reverse)
+{
+    const int n = w.g_off[p] >= 0 ? w.g_n[p] : 0;
+    if (n == 0) return pos;
+    const int lane = threadIdx.x & 31;
+    const int32_t *h = w.gpool + w.g_off[p];
+    const unsigned long long key = prolong_key(w, p >> 1, p & 1);
+    for (int i0 = 0; i0 < n; i0 += 32) {
+        const int i = reverse ? n - 1 - (i0 + lane) : i0 + lane;
+        const bool own = i >= 0 && i < n && w.gkey[h[i]] == key;
+        const unsigned mask = __ballot_sync(kFull, own);
+        if (own) o.hits[pos + __popc(mask & lanemask_lt())] = w.orig[h[i]];
+        pos += __popc(mask);
+    }
+    return pos;
 }
 
 __global__ void __launch_bounds__(256) k_write(const DevConst c, const Workspace w, const OutBuffers o)
@@ -222,22 +242,36 @@ __global__ void __launch_bounds__(256) k_write(const DevConst c, const Workspace
         const unsigned long long key = w.tl_key[t];
         const int n = w.tl_n[t];
         const int32_t *h = w.tl_hits + (int64_t)t * c.nr;
-        if (lane < 5) o.par[(int64_t)m * 5 + lane] = w.tl_par[lane * tcap + t];
-        if (lane < 15) o.cov[(int64_t)m * 15 + lane] = w.tl_cov[lane * tcap + t];
+        // with global tracking, an inward prolongation that fitted clusters gives the state
+        const bool inward = c.global && w.g_n[2 * t] > 0;
+        const float *P = inward ? w.g_par : w.tl_par;
+        const float *V = inward ? w.g_cov : w.tl_cov;
+        if (lane < 5) o.par[(int64_t)m * 5 + lane] = P[lane * tcap + t];
+        if (lane < 15) o.cov[(int64_t)m * 15 + lane] = V[lane * tcap + t];
         if (lane == 0) {
             const int sec = w.starts[t].w >> 16;
-            const int sector = sec % c.ns;
-            o.x[m] = w.tl_x[t];
+            const int sector = inward ? w.g_sec[t] : sec % c.ns;
+            float chi2 = w.tl_chi2[t];
+            int ndf = 2 * n - 5, nhits = w.tl_nowned[t];
+            if (c.global) {
+                chi2 = chi2 + w.g_chi[2 * t];
+                chi2 = chi2 + w.g_chi[2 * t + 1];
+                ndf += 2 * (w.g_n[2 * t] + w.g_n[2 * t + 1]);
+                nhits += w.g_own[2 * t] + w.g_own[2 * t + 1];
+            }
+            o.x[m] = inward ? w.g_x[t] : w.tl_x[t];
             o.alpha[m] = c.sec_alpha[sector];
-            o.chi2[m] = w.tl_chi2[t];
-            o.ndf[m] = 2 * n - 5;
-            o.nhits[m] = w.tl_nowned[t];
+            o.chi2[m] = chi2;
+            o.ndf[m] = ndf;
+            o.nhits[m] = nhits;
             o.first[m] = first;
             o.sector[m] = sector;
             o.event[m] = sec / c.ns;
         }
-        // owned clusters, inner to outer (the tracklet stores them outer to inner)
         int pos = first;
+        // inward prolongation's clusters, inner to outer (found outer to inner)
+        if (c.global) pos = write_prolongation(w, o, 2 * t, pos, true);
+        // owned clusters, inner to outer (the tracklet stores them outer to inner)
         for (int i0 = 0; i0 < n; i0 += 32) {
             const int i = n - 1 - (i0 + lane);
             const bool own = i >= 0 && w.ckey[h[i]] == key;
@@ -245,6 +279,8 @@ __global__ void __launch_bounds__(256) k_write(const DevConst c, const Workspace
             if (own) o.hits[pos + __popc(mask & lanemask_lt())] = w.orig[h[i]];
             pos += __popc(mask);
         }
+        // outward prolongation's clusters, in search order (inner to outer)
+        if (c.global) write_prolongation(w, o, 2 * t + 1, pos, false);
     }
 }
 
@@ -254,7 +290,7 @@ int launch_output(const DevConst &c, const Workspace &w, const OutBuffers &o, in
     const int64_t words = (n_input + 31) / 32 + 1;
     scan<1>(w.bits, w.word_off, words, nullptr, w.scan_tmp, w.counters + CNT_TRACKS, s);
     const int grid = lc.num_sms * 8;
-    k_rank<<<grid, 256, 0, s>>>(w);
+    k_rank<<<grid, 256, 0, s>>>(c, w);
     scan<0>(w.rank_first, w.rank_first, w.tcap, w.counters + CNT_TRACKS, w.scan_tmp, w.counters + CNT_HITS, s);
     k_write<<<grid, 256, 0, s>>>(c, w, o);
     return 8;

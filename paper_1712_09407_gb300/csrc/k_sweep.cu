@@ -367,6 +367,7 @@ __global__ void __launch_bounds__(kSwThreads, 2) k_construct_sweep(const DevCons
                             } else {
                                 KF rs;
                                 sw_load(S, i, rs);
+                                if (c.global) write_outer(w, S.t[i], rs, S.xs[i]);
                                 set_seed_cov(rs, c);
                                 sw_store(S, i, rs);
                                 S.phase[i] = SW_WAIT;
@@ -400,6 +401,7 @@ __global__ void __launch_bounds__(kSwThreads, 2) k_construct_sweep(const DevCons
                     } else {
                         KF rs;
                         sw_load(S, i, rs);
+                        if (c.global) write_outer(w, S.t[i], rs, S.xs[i]);
                         set_seed_cov(rs, c);
                         sw_store(S, i, rs);
                         S.phase[i] = SW_WAIT;

@@ -216,7 +216,8 @@ __device__ __forceinline__ bool seed3(const float x[3], const float y[3], const 
 // within the row, or -1.
 __device__ __forceinline__ int search_cells(const DevConst &c, const float2 *yz, const int32_t *orig,
                                             const int32_t *cell, const float4 gr, int ny, int nz, const KF &pr,
-                                            const Gain &g, float &chi2_out, int &ncand)
+                                            const Gain &g, float &chi2_out, int &ncand,
+                                            const uint8_t *used = nullptr)
 {
     const float wy = c.nsig * sqrtf(pr.c00 + c.sy2);
     const float wz = c.nsig * sqrtf(pr.c11 + c.sz2);
@@ -231,6 +232,7 @@ __device__ __forceinline__ int search_cells(const DevConst &c, const float2 *yz,
         const int a = cell[iz * ny + iy0], e = cell[iz * ny + iy1 + 1];
         ncand += e - a;
         for (int j = a; j < e; j++) {
+            if (used && used[j]) continue;
             const float2 q = yz[j];
             if (!(fabsf(q.x - y) <= wy && fabsf(q.y - z) <= wz)) continue;
             const float x2 = chi2_of(g, q.x - y, q.y - z);
@@ -292,6 +294,67 @@ __device__ __forceinline__ void write_tracklet(const DevConst &c, const Workspac
     } else {
         w.tl_w[t] = -INFINITY;
     }
+}
+
+// State of the outward pass at its last cluster: the track's outer end for global tracking.
+__device__ __forceinline__ void write_outer(const Workspace &w, int t, const KF &st, float xs)
+{
+    const int tcap = (int)w.tcap;
+    float *P = w.tl_opar, *V = w.tl_ocov;
+    P[0 * tcap + t] = st.p0; P[1 * tcap + t] = st.p1; P[2 * tcap + t] = st.p2; P[3 * tcap + t] = st.p3;
+    P[4 * tcap + t] = st.p4;
+    V[0 * tcap + t] = st.c00; V[1 * tcap + t] = st.c10; V[2 * tcap + t] = st.c11; V[3 * tcap + t] = st.c20;
+    V[4 * tcap + t] = st.c21; V[5 * tcap + t] = st.c22; V[6 * tcap + t] = st.c30; V[7 * tcap + t] = st.c31;
+    V[8 * tcap + t] = st.c32; V[9 * tcap + t] = st.c33; V[10 * tcap + t] = st.c40; V[11 * tcap + t] = st.c41;
+    V[12 * tcap + t] = st.c42; V[13 * tcap + t] = st.c43; V[14 * tcap + t] = st.c44;
+    w.tl_ox[t] = xs;
+}
+
+// Change of frame by an azimuth rotation (cos cd, sin sd), same operations as the oracle: the state at
+// x is re-expressed at x' = x cd + y sd (y' = -x sd + y cd, phi' = phi - angle); the covariance is
+// transported with the Jacobian of the map to fixed x'.  False if cos(phi') <= 0 or |sin phi'| >= smax.
+__device__ __forceinline__ bool rotate_state(KF &s, float x, float cd, float sd, const DevConst &c, float &x_new)
+{
+    const float y = s.p0, sp = s.p2;
+    const float cp = sqrtf(__fmaf_rn(-sp, sp, 1.0f));
+    const float xn = __fmaf_rn(x, cd, y * sd);
+    const float yn = __fmaf_rn(y, cd, -(x * sd));
+    const float spn = __fmaf_rn(sp, cd, -(cp * sd));
+    if (!(fabsf(spn) < c.smax)) return false;
+    if (!(__fmaf_rn(cp, cd, sp * sd) > 0.0f)) return false;
+    const float cpn = sqrtf(__fmaf_rn(-spn, spn, 1.0f));
+    const float J00 = __fmaf_rn(-sd, spn / cpn, cd);
+    const float J10 = -(sd * s.p3) / cpn;
+    const float J20 = -(c.kB * s.p4) * sd;
+    const float J22 = cpn / cp;
+    s.p0 = yn;
+    s.p2 = spn;
+    // J C, rows (only rows 0, 1, 2 differ from C)
+    const float C00 = s.c00, C01 = s.c10, C02 = s.c20, C03 = s.c30, C04 = s.c40;
+    const float C11 = s.c11, C12 = s.c21, C13 = s.c31, C14 = s.c41;
+    const float C22 = s.c22, C23 = s.c32, C24 = s.c42;
+    const float JC00 = J00 * C00;    // only column 0 of row 0 enters the lower triangle
+    const float JC10 = __fmaf_rn(1.0f, C01, J10 * C00), JC11 = __fmaf_rn(1.0f, C11, J10 * C01);
+    const float JC12 = __fmaf_rn(1.0f, C12, J10 * C02), JC13 = __fmaf_rn(1.0f, C13, J10 * C03);
+    const float JC14 = __fmaf_rn(1.0f, C14, J10 * C04);
+    const float JC20 = __fmaf_rn(J22, C02, J20 * C00), JC21 = __fmaf_rn(J22, C12, J20 * C01);
+    const float JC22 = __fmaf_rn(J22, C22, J20 * C02), JC23 = __fmaf_rn(J22, C23, J20 * C03);
+    const float JC24 = __fmaf_rn(J22, C24, J20 * C04);
+    // (J C) J^T, lower triangle; rows 3, 4 of J C are rows 3, 4 of C
+    s.c00 = JC00 * J00;
+    s.c10 = JC10 * J00;
+    s.c11 = __fmaf_rn(JC11, 1.0f, JC10 * J10);
+    s.c20 = JC20 * J00;
+    s.c21 = __fmaf_rn(JC21, 1.0f, JC20 * J10);
+    s.c22 = __fmaf_rn(JC22, J22, JC20 * J20);
+    s.c30 = C03 * J00;
+    s.c31 = __fmaf_rn(C13, 1.0f, C03 * J10);
+    s.c32 = __fmaf_rn(C23, J22, C03 * J20);
+    s.c40 = C04 * J00;
+    s.c41 = __fmaf_rn(C14, 1.0f, C04 * J10);
+    s.c42 = __fmaf_rn(C24, J22, C04 * J20);
+    x_new = xn;
+    return true;
 }
 
 // Seed of tracklet t from its chain of kept links (first, middle and last cluster).  Returns false

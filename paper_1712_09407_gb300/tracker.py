@@ -37,7 +37,7 @@ class tpc_params(ctypes.Structure):
                 ("nb_gate", c_float), ("min_chain", c_int), ("seed_cov", c_float * 5),
                 ("win_nsigma", c_float), ("chi2_max", c_float), ("max_miss", c_int),
                 ("edge_margin", c_float), ("sin_max", c_float), ("alpha", c_float), ("beta", c_float),
-                ("min_clusters", c_int), ("qpt_max", c_float)]
+                ("min_clusters", c_int), ("qpt_max", c_float), ("global_tracking", c_int)]
 
 
 class tpc_tuning(ctypes.Structure):
@@ -62,7 +62,8 @@ class tpc_debug_view(ctypes.Structure):
 
 class tpc_call_stats(ctypes.Structure):
     _fields_ = [("ms", c_float * 8), ("kernel_launches", c_int), ("clusters", c_int64), ("tracklets", c_int64),
-                ("row_visits", c_int64), ("candidates", c_int64), ("tracks", c_int64), ("hits", c_int64)]
+                ("row_visits", c_int64), ("candidates", c_int64), ("tracks", c_int64), ("hits", c_int64),
+                ("global_found", c_int64)]
 
 
 EXPORTS = {
@@ -251,9 +252,10 @@ def tpc_tracker_set_timing(tr, enable=True):
 def tpc_result_stats(res) -> dict:
     st = tpc_call_stats()
     _check(lib().tpc_result_stats(res, ctypes.byref(st)), "tpc_result_stats")
-    return dict(ms=list(st.ms)[:7], kernel_launches=st.kernel_launches, clusters=st.clusters,
+    # ms: set-up, ingest, neighbours, evolution, construction, selection, output, global tracking
+    return dict(ms=list(st.ms), kernel_launches=st.kernel_launches, clusters=st.clusters,
                 tracklets=st.tracklets, row_visits=st.row_visits, candidates=st.candidates, tracks=st.tracks,
-                hits=st.hits)
+                hits=st.hits, global_found=st.global_found)
 
 
 def tpc_find_links_noalloc(tr, y, z, row, counts, up, dn, status=None, stream=None, n=None):
@@ -363,7 +365,10 @@ class Tracker:
     """A tracker on the current CUDA device for one geometry."""
 
     def __init__(self, row_x, tan_half=0.17632698070846498, z_max=250.0, n_sectors=36, bz=0.5, params=None,
-                 budget=0, tuning=None):
+                 budget=0, tuning=None, global_tracking=None):
+        if global_tracking is not None:
+            params = params if params is not None else tpc_params_default()
+            params.global_tracking = int(bool(global_tracking))
         self.row_x = np.asarray(row_x, dtype=np.float32)
         self.n_rows = int(self.row_x.shape[0])
         self.n_sectors = int(n_sectors)
