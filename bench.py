@@ -33,7 +33,7 @@ METRIC = "central-like events/s"
 WORKLOAD = ("central-like event: 16000 primary + 3000 secondary helices (vertex radius U[0,60] cm), "
             "pT > 0.05 GeV, 20% noise, 36 sectors x 159 pad rows, Bz 0.5 T, seed 1")
 PROFILE_JSON = os.path.join(ROOT, "profiles", "construct_traffic.json")
-CONSTRUCT_SRC = os.path.join(ROOT, "paper_1712_09407_gb300", "csrc", "k_construct.cu")
+CONSTRUCT_SRC = [os.path.join(ROOT, "paper_1712_09407_gb300", "csrc", f) for f in ("k_construct.cu", "kf.cuh", "common.cuh")]
 
 
 def parse():
@@ -152,11 +152,19 @@ def construct_bytes(stats):
     return V * (16 + 8 + 16 + 8) + 8 * K + T * (16 + 24 + 4 + 100) + 4 * V // 2
 
 
+def construct_source_hash():
+    """Hash of the sources that make up k_construct (its file and the headers it inlines)."""
+    h = hashlib.sha256()
+    for f in CONSTRUCT_SRC:
+        h.update(open(f, "rb").read())
+    return h.hexdigest()[:16]
+
+
 def traffic_for_current_kernel():
     if not os.path.exists(PROFILE_JSON):
         return None, None
     d = json.load(open(PROFILE_JSON))
-    h = hashlib.sha256(open(CONSTRUCT_SRC, "rb").read()).hexdigest()[:16]
+    h = construct_source_hash()
     if d.get("source_sha256_16") != h:
         return None, "kernel changed since capture"
     return d.get("dram_bytes_per_launch"), d.get("note")
@@ -330,6 +338,40 @@ def run_ours(args):
     for t in trackers:
         t.set_timing(False)
 
+    # ---- global tracking (Section 5) on the same events, one at a time, L2 flushed (untimed)
+    gtr = Tracker.for_geometry(ev.geometry, global_tracking=True)
+    gtr.reserve(max(p[4] for p in pool), 1)
+    n_g = min(args.steps, 20)
+    g_ms, g_stats = [], []
+    with torch.cuda.stream(stream):
+        for k in range(args.warmup):
+            d = dev[k % len(dev)]
+            r = gtr.track(d[0], d[1], d[2], d[3], stream=stream)
+            r.sync()
+            r.release()
+        gtr.set_timing(True)
+        for k in range(n_g):
+            d = dev[k % len(dev)]
+            flush.fill_(float(k))
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            r = gtr.track(d[0], d[1], d[2], d[3], stream=stream)
+            b.record(stream)
+            r.sync()
+            g_stats.append(r.stats())
+            r.release()
+            g_ms.append(a.elapsed_time(b))
+    gtr.close()
+    g_stage = np.mean([np.array(s_["ms"]) for s_ in g_stats], axis=0)
+    global_line = {
+        "events_per_s": n_g / (sum(g_ms) / 1e3), "ms_per_event": float(np.mean(g_ms)), "steps": n_g,
+        "stages_ms": {n: round(float(v), 4) for n, v in zip(
+            ["setup", "ingest", "neighbours", "evolution", "construction", "selection", "output", "global"], g_stage)},
+        "clusters_found_per_event": float(np.mean([s_["global_found"] for s_ in g_stats])),
+        "clusters_added_per_event": float(np.mean([g_stats[k]["hits"] - stats_all[k]["hits"] for k in range(n_g)])),
+        "tracks_per_event": float(np.mean([s_["tracks"] for s_ in g_stats])),
+        "l2": "flushed before every event (512 MB write, untimed)"}
+
     # ---- end to end through the host-buffer entry point
     e2e = None
     if not args.no_e2e:
@@ -388,7 +430,7 @@ def run_ours(args):
                            args.resident, args.resident * n_mean * 9 / 1e6),
                        "parallelism": "replicas" if world > 1 else "single GPU"},
             "clusters_per_s": value * n_mean, "tracks_per_event": int(np.mean(tracks)),
-            "one_event_at_a_time": serial, "stages_ms": stages,
+            "one_event_at_a_time": serial, "stages_ms": stages, "global_tracking": global_line,
             "gpu_launches": launches, "e2e": e2e, "roofline": roof, "clocks": clk,
             "wall_s_timed_region": wall}
     if world == 1 and not args.no_cpu_baseline:

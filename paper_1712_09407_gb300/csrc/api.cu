@@ -319,13 +319,13 @@ static size_t carve(tpc_tracker *tr, const WsSizes &s, Alloc &a)
         w.tl_ox = a.take<float>(s.T);
         w.used = a.take<uint8_t>(s.P);
         w.gkey = a.take<unsigned long long>(s.P);
+        w.gent = a.take<int4>(s.P);
         w.gpool = a.take<int32_t>(s.P);
         w.gpool_cap = s.P;
         w.g_off = a.take<int32_t>(2 * s.T);
         w.g_n = a.take<int32_t>(2 * s.T);
         w.g_own = a.take<int32_t>(2 * s.T);
         w.g_chi = a.take<float>(2 * s.T);
-        w.g_list = a.take<int32_t>(2 * s.T);
         w.g_par = a.take<float>(5 * s.T);
         w.g_cov = a.take<float>(15 * s.T);
         w.g_x = a.take<float>(s.T);
@@ -334,14 +334,15 @@ static size_t carve(tpc_tracker *tr, const WsSizes &s, Alloc &a)
         w.tl_opar = w.tl_ocov = w.tl_ox = w.g_chi = w.g_par = w.g_cov = w.g_x = nullptr;
         w.used = nullptr;
         w.gkey = nullptr;
-        w.gpool = w.g_off = w.g_n = w.g_own = w.g_list = w.g_sec = nullptr;
+        w.gent = nullptr;
+        w.gpool = w.g_off = w.g_n = w.g_own = w.g_sec = nullptr;
         w.gpool_cap = 0;
     }
     w.bits = a.take<uint32_t>(s.W);
     w.word_off = a.take<int32_t>(s.W);
     w.rank_trk = a.take<int32_t>(s.T);
     w.rank_first = a.take<int32_t>(s.T);
-    w.scan_tmp = a.take<int32_t>((s.W > s.T ? s.W : s.T) / 4096 + 64);
+    w.scan_tmp = a.take<int32_t>((s.W > 2 * s.T ? s.W : 2 * s.T) / 4096 + 64);
     w.counters = a.take<int32_t>(kCountWords);
     w.err = w.counters + CNT_COUNT;
     w.ncap = s.P;

@@ -27,8 +27,8 @@ enum {
     CNT_VISITS = 4,     // A5 row visits (statistics)
     CNT_CANDS = 5,      // A5 clusters read inside the enumerated grid cells (statistics)
     CNT_SW_CHUNKS = 6,  // chunks of the sector-sweep constructor
-    CNT_GPOOL = 7,      // global tracking: clusters stored in the prolongation pool
-    CNT_GLIST = 8,      // global tracking: prolongations that found clusters
+    CNT_GPOOL = 7,      // global tracking: entries appended to the prolongation pool
+    CNT_GLIST = 8,      // global tracking: prolongations of the call (2 per tracklet)
     CNT_COUNT = 12
 };
 
@@ -91,13 +91,13 @@ struct Workspace {
     float *tl_opar, *tl_ocov, *tl_ox;   // outward pass's state at its last cluster [5|15|1][tcap]
     uint8_t *used;         // [slots] cluster of an accepted track
     unsigned long long *gkey;   // [slots] prolongation claims
-    int32_t *gpool;        // [gpool_cap] clusters found by prolongations
+    int4 *gent;            // [gpool_cap] unordered pool: {slot, prolongation, position in it, 0}
+    int32_t *gpool;        // [gpool_cap] clusters found, per prolongation in search order at g_off
     int64_t gpool_cap;
-    int32_t *g_off, *g_n, *g_own;       // [2 * tcap] per (tracklet, end)
+    int32_t *g_off, *g_n, *g_own;       // [2 * tcap] per prolongation p = 2 * tracklet + (0 in, 1 out)
     float *g_chi;          // [2 * tcap]
     float *g_par, *g_cov, *g_x;         // inward prolongation's last state [5|15|1][tcap]
     int32_t *g_sec;        // [tcap] sector (within the event) of that state
-    int32_t *g_list;       // [2 * tcap] prolongations that found clusters
     // output ordering
     uint32_t *bits;        // bitmap over input indices of innermost clusters
     int32_t *word_off;     // exclusive prefix of popcounts
@@ -217,6 +217,10 @@ int launch_select(const DevConst &c, const Workspace &w, int64_t n_input, const 
 int launch_output(const DevConst &c, const Workspace &w, const OutBuffers &o, int64_t n_input,
                    const LaunchCfg &lc, cudaStream_t s);
 int launch_global(const DevConst &c, const Workspace &w, int64_t n_slots, const LaunchCfg &lc, cudaStream_t s);
+// Exclusive scan of min(n, *n_dev) int32 values (n_dev may be null); total to *total_out if given.
+// partials needs n / 4096 + 64 ints.  Returns the kernels launched.
+int launch_scan_i32(const int32_t *in, int32_t *out, int64_t n, const int32_t *n_dev, int32_t *partials,
+                    int32_t *total_out, cudaStream_t s);
 int neighbours_smem_limit();
 
 // Read-only view of a tracker's constants for entry points defined outside api.cu.

@@ -11,11 +11,11 @@
 // cluster, gives the reported state.
 //
 // The prolongations of a call are few and mostly end at the edge test, so one thread takes one
-// (track, end) pair.  Pass 1 runs every prolongation without storing anything but its count,
-// chi2 and final state, and reserves its range of the pool; pass 2 runs again only the
-// prolongations that found clusters (same inputs, same arithmetic, same clusters) and stores and
-// claims them; pass 3 counts what each prolongation owns.  The track's output assembles the
-// owned clusters inner to outer.
+// (track, end) pair.  A prolongation claims every cluster it finds at once and appends
+// {slot, prolongation, position} to an unordered pool (warp-aggregated atomics); a scan of the
+// per-prolongation counts then gives each prolongation its range, and one pass over the pool
+// puts every entry in place and counts the clusters each prolongation owns.  The track's output
+// assembles the owned clusters inner to outer.
 #include "kf.cuh"
 #include "../../include/tpcca.h"
 
@@ -72,13 +72,28 @@ __device__ __forceinline__ void end_state(const DevConst &c, const Workspace &w,
     r = row_of_x(c, x);
 }
 
-// One prolongation from `end` (at x_end, row r_end, sector `sec` of the call) in direction dir.
-// Returns the clusters found; with STORE the first nmax of them are written to out[] (slots) and
-// claimed with key.
-template <bool STORE>
-__device__ int prolong(const DevConst &c, const Workspace &w, int sec, const KF &end, float x_end, int r_end,
-                       int dir, int32_t *out, int nmax, unsigned long long key, float &chi2_out, KF &fin,
-                       float &x_fin, int &s2_out)
+// Append one entry to the unordered pool; the lanes of a warp that append in the same step share
+// one atomic.  Returns false (and records a capacity error) when the pool is full.
+__device__ __forceinline__ bool pool_append(const DevConst &c, const Workspace &w, int slot, int p, int j, int sec)
+{
+    const unsigned act = __activemask();
+    const int lane = threadIdx.x & 31;
+    const int leader = __ffs(act) - 1;
+    int base = 0;
+    if (lane == leader) base = atomicAdd(&w.counters[CNT_GPOOL], __popc(act));
+    base = __shfl_sync(act, base, leader) + __popc(act & lanemask_lt());
+    if ((int64_t)base >= w.gpool_cap) {
+        set_error(w.err, TPC_ERR_CAPACITY, sec * c.nr, c, TPC_STAGE_GLOBAL);
+        return false;
+    }
+    w.gent[base] = make_int4(slot, p, j, 0);
+    return true;
+}
+
+// One prolongation p = 2 t + d from `end` (at x_end, row r_end, sector `sec` of the call) in
+// direction dir.  Claims and records the clusters it finds; returns their number.
+__device__ int prolong(const DevConst &c, const Workspace &w, int p, int sec, const KF &end, float x_end, int r_end,
+                       int dir, unsigned long long key, float &chi2_out, KF &fin, float &x_fin, int &s2_out)
 {
     chi2_out = 0.0f;
     const int rn = r_end + dir;
@@ -105,27 +120,26 @@ __device__ int prolong(const DevConst &c, const Workspace &w, int sec, const KF 
     int n = 0, miss = 0, cands = 0;
     float chi2sum = 0.0f;
     for (; r >= 0 && r < c.nr; r += dir) {
+        // the row's search record first, so that its latency overlaps the transport
+        const int4 rg = __ldg(&w.rgi[gsec * c.nr + r]);
+        const float4 gr = __ldg(&w.grid[gsec * c.nr + r]);
         const float xr = c.row_x[r];
-        KF p = st;
-        if (!propagate(p, xr - xs, c)) break;
-        if (fabsf(p.p0) > __fmaf_rn(xr, c.th, c.margin)) break;
-        const Gain g = residual_cov_inv(p, c);
-        const int4 rg = w.rgi[gsec * c.nr + r];
-        const float4 gr = w.grid[gsec * c.nr + r];
+        KF q = st;
+        if (!propagate(q, xr - xs, c)) break;
+        if (fabsf(q.p0) > __fmaf_rn(xr, c.th, c.margin)) break;
+        const Gain g = residual_cov_inv(q, c);
         float chi2 = 0.0f;
-        const int bl = search_cells(c, w.yz + rg.x, w.orig + rg.x, w.cell + rg.y, gr, rg.z, rg.w, p, g, chi2, cands,
+        const int bl = search_cells(c, w.yz + rg.x, w.orig + rg.x, w.cell + rg.y, gr, rg.z, rg.w, q, g, chi2, cands,
                                     w.used + rg.x);
         if (bl >= 0 && chi2 <= c.chi2max) {
             const int b = rg.x + bl;
             chi2sum = chi2sum + chi2;
-            const float2 q = w.yz[b];
-            kf_update(p, g, q.x, q.y);
-            st = p;
+            const float2 m = __ldg(w.yz + b);
+            kf_update(q, g, m.x, m.y);
+            st = q;
             xs = xr;
-            if (STORE && n < nmax) {
-                out[n] = b;
-                atomicMax(&w.gkey[b], key);
-            }
+            atomicMax(&w.gkey[b], key);
+            pool_append(c, w, b, p, n, sec);
             n++;
             miss = 0;
         } else if (++miss >= c.max_miss) {
@@ -145,6 +159,7 @@ __global__ void __launch_bounds__(256) k_global_used(const DevConst c, const Wor
     const int T = n_tracklets(w);
     const int lane = threadIdx.x & 31;
     const int nwarps = (gridDim.x * blockDim.x) >> 5;
+    if (blockIdx.x == 0 && threadIdx.x == 0) w.counters[CNT_GLIST] = 2 * T;     // prolongations of the call
     for (int t = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; t < T; t += nwarps) {
         if (w.tl_inner[t] < 0) continue;
         const unsigned long long key = w.tl_key[t];
@@ -155,8 +170,9 @@ __global__ void __launch_bounds__(256) k_global_used(const DevConst c, const Wor
     }
 }
 
-// Pass 1: every prolongation of every accepted track; counts, chi2, final inward state, pool range.
-__global__ void __launch_bounds__(kGlobalBlock) k_global_find(const DevConst c, const Workspace w)
+// Every prolongation of every accepted track: clusters claimed and pooled, count, chi2, final
+// inward state.
+__global__ void __launch_bounds__(kGlobalBlock, 4) k_global_find(const DevConst c, const Workspace w)
 {
     const int T = n_tracklets(w);
     const int tcap = (int)w.tcap;
@@ -164,69 +180,34 @@ __global__ void __launch_bounds__(kGlobalBlock) k_global_find(const DevConst c, 
         const int t = p >> 1, d = p & 1;
         int n = 0;
         float chi = 0.0f;
-        int off = -1;
         if (w.tl_inner[t] >= 0) {
             KF end, fin;
             float xe, xf;
             int re, s2;
             end_state(c, w, t, d, end, xe, re);
             const int sec = w.starts[t].w >> 16;
-            n = prolong<false>(c, w, sec, end, xe, re, d == 0 ? -1 : 1, nullptr, 0, 0ull, chi, fin, xf, s2);
+            n = prolong(c, w, p, sec, end, xe, re, d == 0 ? -1 : 1, prolong_key(w, t, d), chi, fin, xf, s2);
             if (d == 0 && n > 0) {
                 store_state(w.g_par, w.g_cov, tcap, t, fin);
                 w.g_x[t] = xf;
                 w.g_sec[t] = s2;
             }
-            if (n > 0) {
-                const int o = atomicAdd(&w.counters[CNT_GPOOL], n);
-                if ((int64_t)o + n > w.gpool_cap) {
-                    set_error(w.err, TPC_ERR_CAPACITY, sec * c.nr, c, TPC_STAGE_GLOBAL);
-                } else {
-                    off = o;
-                    w.g_list[atomicAdd(&w.counters[CNT_GLIST], 1)] = p;
-                }
-            }
         }
         w.g_n[p] = n;
         w.g_chi[p] = chi;
-        w.g_off[p] = off;
         w.g_own[p] = 0;
     }
 }
 
-// Pass 2: the prolongations that found clusters store and claim them.
-__global__ void __launch_bounds__(kGlobalBlock) k_global_store(const DevConst c, const Workspace w)
+// Pool entries into place (g_off: exclusive scan of g_n) and owned counts.
+__global__ void __launch_bounds__(256) k_global_place(const Workspace w)
 {
-    const int L = w.counters[CNT_GLIST];
-    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < L; i += gridDim.x * blockDim.x) {
-        const int p = w.g_list[i];
-        const int t = p >> 1, d = p & 1;
-        KF end, fin;
-        float xe, xf, chi;
-        int re, s2;
-        end_state(c, w, t, d, end, xe, re);
-        const int sec = w.starts[t].w >> 16;
-        // same inputs and arithmetic as pass 1, so the same g_n[p] clusters (nmax only bounds the writes)
-        prolong<true>(c, w, sec, end, xe, re, d == 0 ? -1 : 1, w.gpool + w.g_off[p], w.g_n[p], prolong_key(w, t, d),
-                      chi, fin, xf, s2);
-    }
-}
-
-// Pass 3: clusters each prolongation owns.
-__global__ void __launch_bounds__(256) k_global_own(const Workspace w)
-{
-    const int L = w.counters[CNT_GLIST];
-    const int lane = threadIdx.x & 31;
-    const int nwarps = (gridDim.x * blockDim.x) >> 5;
-    for (int i = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; i < L; i += nwarps) {
-        const int p = w.g_list[i];
-        const unsigned long long key = prolong_key(w, p >> 1, p & 1);
-        const int n = w.g_n[p];
-        const int32_t *h = w.gpool + w.g_off[p];
-        int own = 0;
-        for (int j = lane; j < n; j += 32) own += (w.gkey[h[j]] == key);
-        for (int o = 16; o > 0; o >>= 1) own += __shfl_xor_sync(kFull, own, o);
-        if (lane == 0) w.g_own[p] = own;
+    const int64_t L = w.counters[CNT_GPOOL] < w.gpool_cap ? w.counters[CNT_GPOOL] : w.gpool_cap;
+    for (int64_t i = blockIdx.x * blockDim.x + threadIdx.x; i < L; i += gridDim.x * blockDim.x) {
+        const int4 e = w.gent[i];
+        const int64_t at = (int64_t)w.g_off[e.y] + e.z;
+        if (at < w.gpool_cap) w.gpool[at] = e.x;          // beyond only after a pool overflow (error set)
+        if (w.gkey[e.x] == prolong_key(w, e.y >> 1, e.y & 1)) atomicAdd(&w.g_own[e.y], 1);
     }
 }
 
@@ -236,10 +217,10 @@ int launch_global(const DevConst &c, const Workspace &w, int64_t n_slots, const 
     cudaMemsetAsync(w.gkey, 0, (size_t)n_slots * sizeof(unsigned long long), s);
     const int grid = lc.num_sms * 8;
     k_global_used<<<grid, 256, 0, s>>>(c, w);
-    k_global_find<<<lc.num_sms * 8, kGlobalBlock, 0, s>>>(c, w);
-    k_global_store<<<lc.num_sms * 2, kGlobalBlock, 0, s>>>(c, w);
-    k_global_own<<<grid, 256, 0, s>>>(w);
-    return 4;
+    k_global_find<<<lc.num_sms * 16, kGlobalBlock, 0, s>>>(c, w);
+    const int scans = launch_scan_i32(w.g_n, w.g_off, 2 * w.tcap, w.counters + CNT_GLIST, w.scan_tmp, nullptr, s);
+    k_global_place<<<grid, 256, 0, s>>>(w);
+    return 3 + scans;
 }
 
 }  // namespace tpc

@@ -137,6 +137,13 @@ static void scan(const void *in, int32_t *out, int64_t n, const int32_t *n_dev, 
     k_scan_apply<MODE><<<(unsigned)nb, kScanThreads, 0, s>>>(in, out, n, n_dev, partials);
 }
 
+int launch_scan_i32(const int32_t *in, int32_t *out, int64_t n, const int32_t *n_dev, int32_t *partials,
+                    int32_t *total_out, cudaStream_t s)
+{
+    scan<0>(in, out, n, n_dev, partials, total_out, s);
+    return 3;
+}
+
 // ---------------------------------------------------------------------------------------------
 // A6
 // ---------------------------------------------------------------------------------------------
@@ -215,7 +222,7 @@ __global__ void __launch_bounds__(256) k_rank(const DevConst c, const Workspace 
 __device__ __forceinline__ int write_prolongation(const Workspace &w, const OutBuffers &o, int p, int pos,
                                                   bool reverse)
 {
-    const int n = w.g_off[p] >= 0 ? w.g_n[p] : 0;
+    const int n = w.g_n[p];
     if (n == 0) return pos;
     const int lane = threadIdx.x & 31;
     const int32_t *h = w.gpool + w.g_off[p];
@@ -269,8 +276,10 @@ __global__ void __launch_bounds__(256) k_write(const DevConst c, const Workspace
             o.event[m] = sec / c.ns;
         }
         int pos = first;
-        // inward prolongation's clusters, inner to outer (found outer to inner)
-        if (c.global) pos = write_prolongation(w, o, 2 * t, pos, true);
+        // inward prolongation's clusters, inner to outer (found outer to inner); skipped when the call
+        // failed (a full prolongation pool leaves holes in it)
+        const bool gok = c.global && w.err[ERR_STATUS] == 0;
+        if (gok) pos = write_prolongation(w, o, 2 * t, pos, true);
         // owned clusters, inner to outer (the tracklet stores them outer to inner)
         for (int i0 = 0; i0 < n; i0 += 32) {
             const int i = n - 1 - (i0 + lane);
@@ -280,7 +289,7 @@ __global__ void __launch_bounds__(256) k_write(const DevConst c, const Workspace
             pos += __popc(mask);
         }
         // outward prolongation's clusters, in search order (inner to outer)
-        if (c.global) write_prolongation(w, o, 2 * t + 1, pos, false);
+        if (gok) write_prolongation(w, o, 2 * t + 1, pos, false);
     }
 }
 
