@@ -143,8 +143,7 @@ def measured_peaks():
 
 
 def construct_bytes(stats):
-    """Algorithmic bytes of one tracklet-construction launch (A5):
-    per row visit 16 B unit metadata + 8 B grid size + 16 B grid origin/scale + 8 B per
+    """Algorithmic bytes of one tracklet-construction launch (A5): per row visit 16 B unit metadata + 8 B grid size + 16 B grid origin/scale + 8 B per
     z-row of cells (2 cell starts) + 8 B per cluster read from the cells; per tracklet a
     16 B start record, three 8 B seed points, 4 B input index, 100 B of results and 4 B per
     fitted cluster (taken as 2 per visit of the inward pass, bounded by the visit count)."""

@@ -117,8 +117,9 @@ k_construct(const DevConst c, const Workspace w)
             visits++;
             const Gain g = residual_cov_inv(pr, c);
             float chi2 = 0.0f;
+            float2 q_unused;      // reloaded below instead: keeping it live costs spills at 80 registers
             const int bl = search_cells(c, w.yz + rg.x, w.orig + rg.x, w.cell + rg.y, gr, rg.z, rg.w, pr, g, chi2,
-                                        cands);
+                                        q_unused, cands);
             const int b = bl < 0 ? -1 : rg.x + bl;
             if (b >= 0 && chi2 <= c.chi2max) {
                 const float2 q = __ldg(w.yz + b);

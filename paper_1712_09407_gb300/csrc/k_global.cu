@@ -129,12 +129,12 @@ __device__ int prolong(const DevConst &c, const Workspace &w, int p, int sec, co
         if (fabsf(q.p0) > __fmaf_rn(xr, c.th, c.margin)) break;
         const Gain g = residual_cov_inv(q, c);
         float chi2 = 0.0f;
-        const int bl = search_cells(c, w.yz + rg.x, w.orig + rg.x, w.cell + rg.y, gr, rg.z, rg.w, q, g, chi2, cands,
+        float2 m;
+        const int bl = search_cells(c, w.yz + rg.x, w.orig + rg.x, w.cell + rg.y, gr, rg.z, rg.w, q, g, chi2, m, cands,
                                     w.used + rg.x);
         if (bl >= 0 && chi2 <= c.chi2max) {
             const int b = rg.x + bl;
             chi2sum = chi2sum + chi2;
-            const float2 m = __ldg(w.yz + b);
             kf_update(q, g, m.x, m.y);
             st = q;
             xs = xr;

@@ -342,9 +342,9 @@ __global__ void __launch_bounds__(kSwThreads, 2) k_construct_sweep(const DevCons
                         visits++;
                         const Gain g = residual_cov_inv(pr, c);
                         float chi2 = 0.0f;
-                        const int bl = n > 0 ? search_cells(c, yz, og, ce, gr, rg.z, rg.w, pr, g, chi2, cands) : -1;
+                        float2 q;
+                        const int bl = n > 0 ? search_cells(c, yz, og, ce, gr, rg.z, rg.w, pr, g, chi2, q, cands) : -1;
                         if (bl >= 0 && chi2 <= c.chi2max) {
-                            const float2 q = yz[bl];
                             if (!up) {
                                 S.chi[i] = S.chi[i] + chi2;
                                 w.tl_hits[(int64_t)S.t[i] * c.nr + S.n[i]] = rg.x + bl;

@@ -213,10 +213,11 @@ __device__ __forceinline__ bool seed3(const float x[3], const float y[3], const 
 // Best cluster of one row for a predicted state: minimum chi2 inside the window, ties to the
 // lower input index.  yz, orig, cell point at the row's slots and cell starts (global memory or a
 // shared-memory copy); gr = {ymin, zmin, 1/dy, 1/dz}, ny, nz its grid.  Returns the slot index
-// within the row, or -1.
+// within the row, or -1; the best cluster's (y, z) in best_yz.  used (optional): clusters with a
+// nonzero byte are skipped.
 __device__ __forceinline__ int search_cells(const DevConst &c, const float2 *yz, const int32_t *orig,
                                             const int32_t *cell, const float4 gr, int ny, int nz, const KF &pr,
-                                            const Gain &g, float &chi2_out, int &ncand,
+                                            const Gain &g, float &chi2_out, float2 &best_yz, int &ncand,
                                             const uint8_t *used = nullptr)
 {
     const float wy = c.nsig * sqrtf(pr.c00 + c.sy2);
@@ -228,6 +229,7 @@ __device__ __forceinline__ int search_cells(const DevConst &c, const float2 *yz,
     const int iz1 = cell1(z + wz + kBinSlack, gr.y, gr.w, nz);
     int best = -1, borig = -1;       // borig: input index of the best slot, loaded on the first tie
     float bc = 0.0f;
+    float2 bq = make_float2(0.0f, 0.0f);
     for (int iz = iz0; iz <= iz1; iz++) {
         const int a = cell[iz * ny + iy0], e = cell[iz * ny + iy1 + 1];
         ncand += e - a;
@@ -239,18 +241,21 @@ __device__ __forceinline__ int search_cells(const DevConst &c, const float2 *yz,
             if (best < 0 || x2 < bc) {
                 best = j;
                 bc = x2;
+                bq = q;
                 borig = -1;
             } else if (x2 == bc) {
                 if (borig < 0) borig = orig[best];
                 const int o = orig[j];
                 if (o < borig) {
                     best = j;
+                    bq = q;
                     borig = o;
                 }
             }
         }
     }
     chi2_out = bc;
+    best_yz = bq;
     return best;
 }
 

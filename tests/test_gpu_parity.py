@@ -1,11 +1,12 @@
 """Parity of the CUDA tracker (through the C ABI) with the float-mode CPU oracle, stage by stage.
 
-Tolerances (the spec contract of the build): link agreement and track-by-track,
+Tolerances: link agreement and track-by-track,
 cluster-by-cluster concordance >= 99.99 %; parameters of matched tracks within 1e-4
 relative (denominators max(|ref|, scale) with scales 1 cm, 1 cm, 1e-3, 1e-3, 1e-2 e/GeV);
 exact cluster lists for matched tracks.  Integer stages (binning, cell starts) must be
-bit-exact.  The float expressions of both sides are evaluated in the same order without
-contraction, so in practice the comparison is exact except where asinf rounds differently.
+bit-exact.  The float expressions of both sides are evaluated in the same order, with the same
+explicit fused multiply-adds and no other contraction, and both use the same arcsin series, so
+in practice the comparison is exact.
 """
 import numpy as np
 import pytest
