@@ -108,6 +108,10 @@ typedef struct {
     int stage_rows;            /* 1: stage rows k-1, k+1 into shared memory with bulk copies */
     int tracklet_capacity;     /* 0: n/4 + 64 per call; > 0: store at most this many tracklets (a capacity
                                   knob: more start hits make the call fail with TPC_ERR_CAPACITY) */
+    int use_graph;             /* 1: every call's copies, clears and kernels are captured into a CUDA graph
+                                  (on a stream of the tracker's own) that updates the tracker's executable
+                                  graph in place and is launched on the call's stream as one unit (default);
+                                  0: plain stream launches.  Same work, same results. */
 } tpc_tuning;
 
 typedef struct tpc_tracker tpc_tracker;
@@ -242,6 +246,7 @@ typedef struct {
     int64_t tracks;                /* output tracks */
     int64_t hits;                  /* output clusters */
     int64_t global_found;          /* clusters found by the global-tracking prolongations (before claims) */
+    int64_t graph_builds;          /* executable graphs the tracker instantiated up to this call (graph mode) */
 } tpc_call_stats;
 
 /* Host-side fault injection for failure tests; no GPU fault is involved.  what = 0: off;

@@ -73,6 +73,10 @@ struct tpc_tracker {
     int64_t last_units = 0, last_slots = 0, last_n = 0;
     bool timing = false;
     int last_err[4] = {0, 0, 0, 0};
+    // graph mode (tuning.use_graph)
+    cudaStream_t cap_stream = nullptr;
+    cudaGraphExec_t gexec = nullptr;
+    int64_t graph_builds = 0;
     std::mutex mu;
 };
 
@@ -89,6 +93,7 @@ struct tpc_result {
     int64_t n_tracks = 0, n_hits = 0;
     int64_t n_clusters = 0;
     int launches = 0;
+    int64_t graph_builds = 0;            // the tracker's graph instantiations up to this call
     bool timed = false;
     cudaEvent_t stage_ev[9] = {};
 };
@@ -161,6 +166,7 @@ extern "C" void tpc_tuning_default(tpc_tuning *t)
     t->construct_mode = 0;
     t->stage_rows = 1;
     t->tracklet_capacity = 0;
+    t->use_graph = 1;
 }
 
 extern "C" const char *tpc_status_string(int s)
@@ -261,7 +267,7 @@ extern "C" int tpc_tracker_set_tuning(tpc_tracker *tr, const tpc_tuning *t)
     if (!(t->bin_occupancy >= 0.5f) || t->neighbours_block < 32 || t->neighbours_block > 256 ||
         t->neighbours_block % 32 || t->construct_block < 32 || t->construct_block > 128 ||
         t->construct_block % 32 || t->construct_ctas_per_sm < 0 || t->construct_mode < 0 || t->construct_mode > 1 ||
-        t->tracklet_capacity < 0)
+        t->tracklet_capacity < 0 || t->use_graph < 0 || t->use_graph > 1)
         return TPC_ERR_INVALID_ARG;
     tr->tuning = *t;
     return TPC_OK;
@@ -555,15 +561,6 @@ static int run(tpc_tracker *tr, const float *y, const float *z, const uint8_t *r
     Workspace wk = tr->w;
     if (tr->tuning.tracklet_capacity > 0 && tr->tuning.tracklet_capacity < wk.tcap) wk.tlim = tr->tuning.tracklet_capacity;
     const Workspace &w = wk;
-    if (R > 0) {
-        TPC_CUDA(cudaMemcpyAsync(w.meta, sg.meta, R * sizeof(int4), cudaMemcpyHostToDevice, st));
-        TPC_CUDA(cudaMemcpyAsync(w.dims, sg.dims, R * sizeof(int2), cudaMemcpyHostToDevice, st));
-    }
-    TPC_CUDA(cudaEventRecord(sg.consumed, st));
-    sg.pending = true;
-    TPC_CUDA(cudaMemsetAsync(w.counters, 0, kCountWords * sizeof(int32_t), st));
-    TPC_CUDA(cudaMemsetAsync(w.bits, 0, ((n_total + 31) / 32 + 2) * sizeof(uint32_t), st));
-    TPC_CUDA(cudaMemsetAsync(w.ckey, 0, s_off * sizeof(unsigned long long), st));
 
     LaunchCfg lc;
     lc.num_sms = tr->num_sms;
@@ -574,28 +571,75 @@ static int run(tpc_tracker *tr, const float *y, const float *z, const uint8_t *r
     lc.stage_rows = tr->tuning.stage_rows;
     lc.neighbours_smem_max = smem;
 
-    int launches = 0;
-    auto mark = [&](int i) {
-        if (timed) cudaEventRecord(res->stage_ev[i], st);
+    // The call's copies, clears and launches go to the caller's stream, or (graph mode) are
+    // captured on the tracker's own stream into a graph that updates the cached executable graph
+    // in place and is launched on the caller's stream as one unit.
+    const bool graph = tr->tuning.use_graph != 0;
+    cudaStream_t ls = st;
+    if (graph) {
+        if (!tr->cap_stream) TPC_CUDA(cudaStreamCreateWithFlags(&tr->cap_stream, cudaStreamNonBlocking));
+        ls = tr->cap_stream;
+        TPC_CUDA(cudaStreamBeginCapture(ls, cudaStreamCaptureModeThreadLocal));
+    }
+    cudaError_t ce = cudaSuccess;
+    auto chk = [&](cudaError_t e) {
+        if (ce == cudaSuccess && e != cudaSuccess) ce = e;
     };
+    auto mark = [&](int i) {
+        if (timed)
+            chk(graph ? cudaEventRecordWithFlags(res->stage_ev[i], ls, cudaEventRecordExternal)
+                      : cudaEventRecord(res->stage_ev[i], ls));
+    };
+    if (R > 0) {
+        chk(cudaMemcpyAsync(w.meta, sg.meta, R * sizeof(int4), cudaMemcpyHostToDevice, ls));
+        chk(cudaMemcpyAsync(w.dims, sg.dims, R * sizeof(int2), cudaMemcpyHostToDevice, ls));
+    }
+    if (!graph) chk(cudaEventRecord(sg.consumed, st));
+    chk(cudaMemsetAsync(w.counters, 0, kCountWords * sizeof(int32_t), ls));
+    chk(cudaMemsetAsync(w.bits, 0, ((n_total + 31) / 32 + 2) * sizeof(uint32_t), ls));
+    chk(cudaMemsetAsync(w.ckey, 0, s_off * sizeof(unsigned long long), ls));
+
+    int launches = 0;
     mark(1);
-    launches += launch_ingest(tr->dc, w, y, z, row, R, st);
+    launches += launch_ingest(tr->dc, w, y, z, row, R, ls);
     mark(2);
-    launches += launch_neighbours(tr->dc, w, R, smem, lc, st);
+    launches += launch_neighbours(tr->dc, w, R, smem, lc, ls);
     mark(3);
-    launches += launch_evolve(tr->dc, w, R, st);
+    launches += launch_evolve(tr->dc, w, R, ls);
     mark(4);
-    launches += lc.construct_mode == 1 ? launch_construct_sweep(tr->dc, w, (int)(R / nr), lc, st)
-                                       : launch_construct(tr->dc, w, lc, st);
+    launches += lc.construct_mode == 1 ? launch_construct_sweep(tr->dc, w, (int)(R / nr), lc, ls)
+                                       : launch_construct(tr->dc, w, lc, ls);
     mark(5);
-    launches += launch_select(tr->dc, w, n_total, lc, st);
+    launches += launch_select(tr->dc, w, n_total, lc, ls);
     mark(6);
-    if (tr->dc.global) launches += launch_global(tr->dc, w, s_off, lc, st);
+    if (tr->dc.global) launches += launch_global(tr->dc, w, s_off, lc, ls);
     mark(8);
-    launches += launch_output(tr->dc, w, res->out, n_total, lc, st);
+    launches += launch_output(tr->dc, w, res->out, n_total, lc, ls);
     mark(7);
-    TPC_CUDA(cudaGetLastError());
+    chk(cudaGetLastError());
+    if (graph) {
+        cudaGraph_t g = nullptr;
+        chk(cudaStreamEndCapture(ls, &g));
+        if (ce == cudaSuccess && tr->gexec) {
+            cudaGraphExecUpdateResultInfo info;
+            if (cudaGraphExecUpdate(tr->gexec, g, &info) != cudaSuccess) {
+                cudaGetLastError();              // a different topology: instantiate anew
+                cudaGraphExecDestroy(tr->gexec);
+                tr->gexec = nullptr;
+            }
+        }
+        if (ce == cudaSuccess && !tr->gexec) {
+            chk(cudaGraphInstantiate(&tr->gexec, g, 0));
+            tr->graph_builds++;
+        }
+        if (ce == cudaSuccess) chk(cudaGraphLaunch(tr->gexec, st));
+        if (g) cudaGraphDestroy(g);
+        if (ce == cudaSuccess) chk(cudaEventRecord(sg.consumed, st));
+    }
+    sg.pending = true;
+    TPC_CUDA(ce);
     res->launches = launches;
+    res->graph_builds = tr->graph_builds;
     TPC_CUDA(cudaMemcpyAsync(res->h_counts, w.counters, kCountWords * sizeof(int32_t), cudaMemcpyDeviceToHost, st));
     TPC_CUDA(cudaEventRecord(res->done, st));
     TPC_CUDA(cudaEventRecord(tr->ws_done, st));
@@ -793,6 +837,10 @@ extern "C" void tpc_tracker_destroy(tpc_tracker *tr)
         }
         if (tr->ws_done) cudaEventDestroy(tr->ws_done);
         tr->ws_done = nullptr;
+        if (tr->gexec) cudaGraphExecDestroy(tr->gexec);
+        if (tr->cap_stream) cudaStreamDestroy(tr->cap_stream);
+        tr->gexec = nullptr;
+        tr->cap_stream = nullptr;
         now = tr->live_results == 0;
     }
     // results still held by the caller keep the (device-free) tracker object alive until released
@@ -842,6 +890,7 @@ extern "C" int tpc_result_stats(tpc_result *r, tpc_call_stats *st)
     st->tracks = r->h_counts[CNT_TRACKS];
     st->hits = r->h_counts[CNT_HITS];
     st->global_found = r->h_counts[CNT_GPOOL];
+    st->graph_builds = r->graph_builds;
     return TPC_OK;
 }
 

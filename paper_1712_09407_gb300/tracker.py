@@ -43,7 +43,7 @@ class tpc_params(ctypes.Structure):
 class tpc_tuning(ctypes.Structure):
     _fields_ = [("bin_occupancy", c_float), ("neighbours_block", c_int), ("construct_block", c_int),
                 ("construct_ctas_per_sm", c_int), ("construct_mode", c_int), ("stage_rows", c_int),
-                ("tracklet_capacity", c_int)]
+                ("tracklet_capacity", c_int), ("use_graph", c_int)]
 
 
 class tpc_track_view(ctypes.Structure):
@@ -63,7 +63,7 @@ class tpc_debug_view(ctypes.Structure):
 class tpc_call_stats(ctypes.Structure):
     _fields_ = [("ms", c_float * 8), ("kernel_launches", c_int), ("clusters", c_int64), ("tracklets", c_int64),
                 ("row_visits", c_int64), ("candidates", c_int64), ("tracks", c_int64), ("hits", c_int64),
-                ("global_found", c_int64)]
+                ("global_found", c_int64), ("graph_builds", c_int64)]
 
 
 EXPORTS = {
@@ -255,7 +255,7 @@ def tpc_result_stats(res) -> dict:
     # ms: set-up, ingest, neighbours, evolution, construction, selection, output, global tracking
     return dict(ms=list(st.ms), kernel_launches=st.kernel_launches, clusters=st.clusters,
                 tracklets=st.tracklets, row_visits=st.row_visits, candidates=st.candidates, tracks=st.tracks,
-                hits=st.hits, global_found=st.global_found)
+                hits=st.hits, global_found=st.global_found, graph_builds=st.graph_builds)
 
 
 def tpc_find_links_noalloc(tr, y, z, row, counts, up, dn, status=None, stream=None, n=None):

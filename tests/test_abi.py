@@ -60,8 +60,8 @@ def test_library_defaults_match_oracle_defaults():
     for f in ("sigma_y", "sigma_z", "nb_ty", "nb_tz", "nb_gate", "win_nsigma", "chi2_max", "edge_margin",
               "sin_max", "alpha", "beta", "qpt_max"):
         assert np.float32(getattr(p, f)) == np.float32(getattr(c, f)), f
-    for f in ("min_chain", "max_miss", "min_clusters"):
-        assert getattr(p, f) == getattr(c, f), f
+    for f in ("min_chain", "max_miss", "min_clusters", "global_tracking"):
+        assert int(getattr(p, f)) == int(getattr(c, f)), f
     assert [np.float32(v) for v in p.seed_cov] == [np.float32(v) for v in c.seed_cov]
 
 
