@@ -71,15 +71,19 @@ class _Cfg(ctypes.Structure):
         ("alpha", ctypes.c_double), ("beta", ctypes.c_double), ("min_clusters", ctypes.c_int),
         ("qpt_max", ctypes.c_double), ("bin_dy", ctypes.c_double), ("bin_dz", ctypes.c_double),
         ("brute_force", ctypes.c_int), ("n_threads", ctypes.c_int), ("global_tracking", ctypes.c_int),
+        ("merge", ctypes.c_int), ("merge_chi2", ctypes.c_double), ("merge_gap", ctypes.c_double),
+        ("merge_qpt_nsigma", ctypes.c_double),
     ]
 
 
 INFO = ["n", "n_starts", "n_tracks", "n_track_hits", "n_rows", "visits", "candidates", "in_window",
-        "nb_candidates", "updates"]
+        "nb_candidates", "updates", "n_merged", "n_merged_hits"]
 PTRS = ["up_raw", "dn_raw", "up", "dn", "starts", "tl_nhits", "tl_ndf", "tl_nup", "tl_hits",
         "tl_par", "tl_cov", "tl_x", "tl_chi2", "tl_w", "owner", "tl_nowned", "tl_accept",
         "trk_tracklet", "trk_first", "trk_nhits", "trk_hits", "trk_par", "trk_cov", "trk_x", "trk_chi2",
-        "trk_ndf", "trk_sector", "trk_nglobal"]
+        "trk_ndf", "trk_sector", "trk_nglobal", "rf_par", "rf_cov", "rf_x", "rf_chi2", "rf_ok", "mg_next",
+        "mrg_first", "mrg_nhits", "mrg_nseg", "mrg_head", "mrg_hits", "mrg_par", "mrg_cov", "mrg_x", "mrg_chi2",
+        "mrg_ndf", "mrg_sector", "mrg_ok"]
 
 
 def lib():
@@ -102,6 +106,8 @@ def lib():
             L.orc_rotate_f64.restype = ctypes.c_int
             L.orc_rotate_f64.argtypes = [P, P, ctypes.c_double, ctypes.c_double, ctypes.c_double, ctypes.c_double,
                                          ctypes.c_double, P]
+            L.orc_chi2_5_f64.restype = ctypes.c_int
+            L.orc_chi2_5_f64.argtypes = [P, P, P]
             L.orc_seed_f64.restype = ctypes.c_int
             L.orc_seed_f64.argtypes = [P, P, P, ctypes.c_double, ctypes.c_double, P]
             L.orc_asin_ratio_f32.restype = ctypes.c_float
@@ -142,6 +148,10 @@ class Config:
     brute_force: bool = False
     n_threads: int = 0
     global_tracking: bool = False
+    merge: bool = False
+    merge_chi2: float = 25.0
+    merge_gap: float = 40.0
+    merge_qpt_nsigma: float = 5.0
 
     def _c(self):
         rx = np.ascontiguousarray(self.row_x, dtype=np.float64)
@@ -149,12 +159,14 @@ class Config:
         c.n_rows = rx.shape[0]
         c.row_x = rx.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
         for f in ("tan_half", "bz", "sigma_y", "sigma_z", "nb_ty", "nb_tz", "nb_gate", "win_nsigma",
-                  "chi2_max", "edge_margin", "sin_max", "alpha", "beta", "qpt_max", "bin_dy", "bin_dz"):
+                  "chi2_max", "edge_margin", "sin_max", "alpha", "beta", "qpt_max", "bin_dy", "bin_dz",
+                  "merge_chi2", "merge_gap", "merge_qpt_nsigma"):
             setattr(c, f, float(getattr(self, f)))
         for f in ("n_sectors", "min_chain", "max_miss", "min_clusters", "n_threads"):
             setattr(c, f, int(getattr(self, f)))
         c.brute_force = int(bool(self.brute_force))
         c.global_tracking = int(bool(self.global_tracking))
+        c.merge = int(bool(self.merge))
         for i in range(5):
             c.seed_cov[i] = float(self.seed_cov[i])
         return c, rx
@@ -198,10 +210,34 @@ class Result:
     trk_ndf: np.ndarray
     trk_sector: np.ndarray
     trk_nglobal: np.ndarray      # clusters added by global tracking
+    # track merger (zero-length unless Config.merge): refit of every sector track ...
+    rf_par: np.ndarray           # [M, 5] at the innermost cluster (frame: its sector)
+    rf_cov: np.ndarray
+    rf_x: np.ndarray
+    rf_chi2: np.ndarray
+    rf_ok: np.ndarray
+    mg_next: np.ndarray          # [M] track merged onto this one's outer end, -1 if none
+    # ... and the merged tracks (one per chain of merged sector tracks, in canonical order)
+    mrg_first: np.ndarray
+    mrg_nhits: np.ndarray
+    mrg_nseg: np.ndarray         # sector tracks merged
+    mrg_head: np.ndarray         # index of the chain's first sector track
+    mrg_hits: np.ndarray
+    mrg_par: np.ndarray
+    mrg_cov: np.ndarray
+    mrg_x: np.ndarray
+    mrg_chi2: np.ndarray
+    mrg_ndf: np.ndarray
+    mrg_sector: np.ndarray
+    mrg_ok: np.ndarray
 
     def track_hits(self, i: int) -> np.ndarray:
         f = self.trk_first[i]
         return self.trk_hits[f:f + self.trk_nhits[i]]
+
+    def merged_hits(self, i: int) -> np.ndarray:
+        f = self.mrg_first[i]
+        return self.mrg_hits[f:f + self.mrg_nhits[i]]
 
     def tracklet_hits(self, t: int) -> np.ndarray:
         return self.tl_hits[t, :self.tl_nhits[t]]
@@ -227,6 +263,8 @@ def track_event(cfg: Config, y, z, row, counts, precision: int = 32) -> Result:
         L.orc_result_ptrs(h, ptrs)
         d = dict(zip(INFO, (int(v) for v in info)))
         N, T, M, H, nr = d["n"], d["n_starts"], d["n_tracks"], d["n_track_hits"], d["n_rows"]
+        Mm, Hm = d["n_merged"], d["n_merged_hits"]
+        Mr = M if cfg.merge else 0
 
         def arr(name, ctype, count, dtype):
             p = ptrs[PTRS.index(name)]
@@ -256,6 +294,18 @@ def track_event(cfg: Config, y, z, row, counts, precision: int = 32) -> Result:
             trk_x=arr("trk_x", f64, M, np.float64), trk_chi2=arr("trk_chi2", f64, M, np.float64),
             trk_ndf=arr("trk_ndf", i32, M, np.int32), trk_sector=arr("trk_sector", i32, M, np.int32),
             trk_nglobal=arr("trk_nglobal", i32, M, np.int32),
+            rf_par=arr("rf_par", f64, Mr * 5, np.float64).reshape(Mr, 5),
+            rf_cov=arr("rf_cov", f64, Mr * 15, np.float64).reshape(Mr, 15),
+            rf_x=arr("rf_x", f64, Mr, np.float64), rf_chi2=arr("rf_chi2", f64, Mr, np.float64),
+            rf_ok=arr("rf_ok", i32, Mr, np.int32), mg_next=arr("mg_next", i32, Mr, np.int32),
+            mrg_first=arr("mrg_first", i32, Mm, np.int32), mrg_nhits=arr("mrg_nhits", i32, Mm, np.int32),
+            mrg_nseg=arr("mrg_nseg", i32, Mm, np.int32), mrg_head=arr("mrg_head", i32, Mm, np.int32),
+            mrg_hits=arr("mrg_hits", i32, Hm, np.int32),
+            mrg_par=arr("mrg_par", f64, Mm * 5, np.float64).reshape(Mm, 5),
+            mrg_cov=arr("mrg_cov", f64, Mm * 15, np.float64).reshape(Mm, 15),
+            mrg_x=arr("mrg_x", f64, Mm, np.float64), mrg_chi2=arr("mrg_chi2", f64, Mm, np.float64),
+            mrg_ndf=arr("mrg_ndf", i32, Mm, np.int32), mrg_sector=arr("mrg_sector", i32, Mm, np.int32),
+            mrg_ok=arr("mrg_ok", i32, Mm, np.int32),
         )
     finally:
         L.orc_result_free(h)
@@ -292,6 +342,16 @@ def seed(x3, y3, z3, bz=0.5, sin_max=0.99):
     st = np.zeros(5)
     ok = L.orc_seed_f64(x3.ctypes.data, y3.ctypes.data, z3.ctypes.data, float(bz), float(sin_max), st.ctypes.data)
     return bool(ok), st
+
+
+def chi2_5(cov15, d):
+    """The merger's 5-parameter chi2 d^T A^-1 d (double precision); None if A is not positive definite."""
+    L = lib()
+    a = np.ascontiguousarray(cov15, dtype=np.float64)
+    dd = np.ascontiguousarray(d, dtype=np.float64)
+    out = np.zeros(1)
+    ok = L.orc_chi2_5_f64(a.ctypes.data, dd.ctypes.data, out.ctypes.data)
+    return float(out[0]) if ok else None
 
 
 def asin_ratio_f32(u: float) -> float:

@@ -38,6 +38,10 @@ void orc_default_config(orc_config *c, const double *row_x, int n_rows, int n_se
     c->brute_force = 0;
     c->n_threads = 0;
     c->global_tracking = 0;
+    c->merge = 0;
+    c->merge_chi2 = 25.0;
+    c->merge_gap = 40.0;
+    c->merge_qpt_nsigma = 5.0;
 }
 
 orc_result *orc_result_alloc(int64_t n, int n_rows)
@@ -98,6 +102,8 @@ void orc_result_info(const orc_result *r, int64_t *info)
     info[ORC_INFO_N_TRACKS] = r->n_tracks;
     info[ORC_INFO_N_TRACK_HITS] = r->n_track_hits;
     info[ORC_INFO_N_ROWS] = r->n_rows;
+    info[ORC_INFO_N_MERGED] = r->n_merged;
+    info[ORC_INFO_N_MERGED_HITS] = r->n_merged_hits;
 }
 
 void orc_result_ptrs(const orc_result *r, void **p)
@@ -130,6 +136,24 @@ void orc_result_ptrs(const orc_result *r, void **p)
     p[ORC_PTR_TRK_NDF] = r->trk_ndf;
     p[ORC_PTR_TRK_SECTOR] = r->trk_sector;
     p[ORC_PTR_TRK_NGLOBAL] = r->trk_nglobal;
+    p[ORC_PTR_RF_PAR] = r->rf_par;
+    p[ORC_PTR_RF_COV] = r->rf_cov;
+    p[ORC_PTR_RF_X] = r->rf_x;
+    p[ORC_PTR_RF_CHI2] = r->rf_chi2;
+    p[ORC_PTR_RF_OK] = r->rf_ok;
+    p[ORC_PTR_MG_NEXT] = r->mg_next;
+    p[ORC_PTR_MRG_FIRST] = r->mrg_first;
+    p[ORC_PTR_MRG_NHITS] = r->mrg_nhits;
+    p[ORC_PTR_MRG_NSEG] = r->mrg_nseg;
+    p[ORC_PTR_MRG_HEAD] = r->mrg_head;
+    p[ORC_PTR_MRG_HITS] = r->mrg_hits;
+    p[ORC_PTR_MRG_PAR] = r->mrg_par;
+    p[ORC_PTR_MRG_COV] = r->mrg_cov;
+    p[ORC_PTR_MRG_X] = r->mrg_x;
+    p[ORC_PTR_MRG_CHI2] = r->mrg_chi2;
+    p[ORC_PTR_MRG_NDF] = r->mrg_ndf;
+    p[ORC_PTR_MRG_SECTOR] = r->mrg_sector;
+    p[ORC_PTR_MRG_OK] = r->mrg_ok;
 }
 
 void orc_result_free(orc_result *r)
@@ -143,5 +167,9 @@ void orc_result_free(orc_result *r)
     free(r->tl_opar); free(r->tl_ocov); free(r->tl_ox); free(r->tl_orow);
     free(r->trk_par); free(r->trk_cov); free(r->trk_x); free(r->trk_chi2);
     free(r->trk_ndf); free(r->trk_sector); free(r->trk_nglobal);
+    free(r->rf_par); free(r->rf_cov); free(r->rf_x); free(r->rf_chi2); free(r->rf_ok); free(r->mg_next);
+    free(r->mrg_first); free(r->mrg_nhits); free(r->mrg_nseg); free(r->mrg_head); free(r->mrg_hits);
+    free(r->mrg_par); free(r->mrg_cov); free(r->mrg_x); free(r->mrg_chi2); free(r->mrg_ndf);
+    free(r->mrg_sector); free(r->mrg_ok);
     free(r);
 }

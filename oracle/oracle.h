@@ -52,6 +52,11 @@ typedef struct {
     int brute_force;          /* 1: every search scans whole rows instead of grid bins */
     int n_threads;            /* OpenMP threads over sectors (<=0: runtime default) */
     int global_tracking;      /* 1: prolong tracks across sector edges (Section 5) */
+    /* track merger with refit (Sections 1 and 3.3) */
+    int merge;                /* 1: refit every track from its clusters and merge across sector borders */
+    double merge_chi2;        /* 5-parameter chi2 gate of a merge */
+    double merge_gap;         /* largest radial gap (cm) between the merged ends */
+    double merge_qpt_nsigma;  /* q/pT gate in combined sigmas */
 } orc_config;
 
 /* Result of one event.  Indices of clusters are input ("original") indices. */
@@ -68,6 +73,8 @@ enum {
     ORC_INFO_IN_WINDOW,       /* construction clusters inside the search window */
     ORC_INFO_NB_CANDIDATES,   /* neighbours finder clusters inside bin ranges (both rows) */
     ORC_INFO_UPDATES,         /* construction Kalman updates (both passes) */
+    ORC_INFO_N_MERGED,        /* tracks after the merger */
+    ORC_INFO_N_MERGED_HITS,
     ORC_INFO_COUNT
 };
 
@@ -85,6 +92,12 @@ enum {
     ORC_PTR_TRK_PAR, ORC_PTR_TRK_COV, ORC_PTR_TRK_X, ORC_PTR_TRK_CHI2,    /* double [M*5], [M*15], [M], [M] */
     ORC_PTR_TRK_NDF, ORC_PTR_TRK_SECTOR,                                 /* int32 [M]: frame sector of par */
     ORC_PTR_TRK_NGLOBAL,                                                 /* int32 [M]: clusters added by global tracking */
+    ORC_PTR_RF_PAR, ORC_PTR_RF_COV, ORC_PTR_RF_X, ORC_PTR_RF_CHI2,        /* double [M*5], [M*15], [M], [M]: refits */
+    ORC_PTR_RF_OK, ORC_PTR_MG_NEXT,                                      /* int32 [M] */
+    ORC_PTR_MRG_FIRST, ORC_PTR_MRG_NHITS, ORC_PTR_MRG_NSEG, ORC_PTR_MRG_HEAD, /* int32 [Mm] */
+    ORC_PTR_MRG_HITS,                                                    /* int32 [sum] */
+    ORC_PTR_MRG_PAR, ORC_PTR_MRG_COV, ORC_PTR_MRG_X, ORC_PTR_MRG_CHI2,    /* double */
+    ORC_PTR_MRG_NDF, ORC_PTR_MRG_SECTOR, ORC_PTR_MRG_OK,                 /* int32 [Mm] */
     ORC_PTR_COUNT
 };
 
@@ -115,6 +128,9 @@ float orc_asin_ratio_f32(float u);
  * if the direction does not point to increasing x in the new frame.  *x_new receives x'. */
 int orc_rotate_f64(double *state, double *cov15, double x, double cos_d, double sin_d, double bz, double sin_max,
                    double *x_new);
+/* chi2 = d^T A^-1 d of the merger's match (A: 5x5 lower triangle, row-major); returns 0 if A is
+ * not positive definite. */
+int orc_chi2_5_f64(const double *A15, const double *d5, double *chi2);
 /* Seed state from three (x, y, z) points (first, middle, last of a chain). */
 int orc_seed_f64(const double *x3, const double *y3, const double *z3, double bz, double sin_max,
                  double *state);

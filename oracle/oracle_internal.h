@@ -21,6 +21,12 @@ struct orc_result {
     int32_t *tl_orow;
     double *trk_par, *trk_cov, *trk_x, *trk_chi2;
     int32_t *trk_ndf, *trk_sector, *trk_nglobal;
+    /* track merger: refit of every sector track, outward partner, merged tracks */
+    double *rf_par, *rf_cov, *rf_x, *rf_chi2;
+    int32_t *rf_ok, *mg_next;
+    int64_t n_merged, n_merged_hits;
+    int32_t *mrg_first, *mrg_nhits, *mrg_nseg, *mrg_head, *mrg_hits, *mrg_ndf, *mrg_sector, *mrg_ok;
+    double *mrg_par, *mrg_cov, *mrg_x, *mrg_chi2;
 };
 
 orc_result *orc_result_alloc(int64_t n, int n_rows);

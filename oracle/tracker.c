@@ -93,6 +93,9 @@ typedef struct {
     int global;
     real c20, s20;                /* cos, sin of the 20 degree sector pitch */
     int ns;
+    int merge;                    /* track merger with refit */
+    real crot[18], srot[18];      /* cos, sin of d * 20 degrees (d = 0..17, read as -160..180) */
+    real mchi2, mgap, mq2;        /* merger gates: chi2, radial gap, (q/pT sigmas)^2 */
 } K;
 
 static void make_consts(K *k, const orc_config *c)
@@ -128,6 +131,16 @@ static void make_consts(K *k, const orc_config *c)
     k->c20 = (real)cos(20.0 * 3.14159265358979323846 / 180.0);
     k->s20 = (real)sin(20.0 * 3.14159265358979323846 / 180.0);
     k->ns = c->n_sectors;
+    k->merge = c->merge && c->n_sectors == 36;
+    for (int d = 0; d < 18; d++) {
+        int deg = d <= 9 ? 20 * d : 20 * (d - 18);          /* -160 .. 180 */
+        double a = (double)(deg < 0 ? -deg : deg) * 3.14159265358979323846 / 180.0;
+        k->crot[d] = (real)cos(a);
+        k->srot[d] = deg < 0 ? -(real)sin(a) : (real)sin(a);
+    }
+    k->mchi2 = (real)c->merge_chi2;
+    k->mgap = (real)c->merge_gap;
+    k->mq2 = (real)(c->merge_qpt_nsigma * c->merge_qpt_nsigma);
 }
 
 /* ----------------------------------------------------------------------------------------- */
@@ -740,6 +753,300 @@ static int prolong(Sector *S, const K *k, const real *Y, const real *Zc, int s, 
     return n;
 }
 
+/* ----------------------------------------------------------------------------------------- */
+/* Track merger with refit (Section 1: "the sector tracks are merged by the track merger";      */
+/* Section 3.3: the merger refits every track from its cluster list alone, so equal cluster     */
+/* lists give bitwise equal results whatever rounding the sector tracker saw)                   */
+/* ----------------------------------------------------------------------------------------- */
+
+/* Steps of 20 degrees that take frame `from` to frame `to` (0..17; same azimuth: 0). */
+static int rot_steps(int from, int to) { return ((to % 18) - (from % 18) + 18) % 18; }
+
+/* Frame change of the state for the cluster's sector; returns 0 if the rotation fails. */
+static int to_frame(const K *k, KS *st, real *xs, int *sc, int s_new)
+{
+    int d = rot_steps(*sc, s_new);
+    *sc = s_new;
+    if (d == 0) return 1;                 /* same azimuth (also the other z half): same frame */
+    real xn;
+    if (!rotate(st, *xs, k->crot[d], k->srot[d], k->kB, k->smax, &xn)) return 0;
+    *xs = xn;
+    return 1;
+}
+
+/* One Kalman pass over the clusters h[i0], h[i0 + dir], ... (n of them) from the state st at
+ * (xs, sector sc); every cluster is used (no search).  chi2 of the updates is summed. */
+static int refit_pass(const K *k, const real *Y, const real *Zc, const uint8_t *rowv, const int32_t *secv,
+                      const int32_t *h, int n, int dir, KS *st, real *xs, int *sc, real *chi2sum)
+{
+    Gain g;
+    for (int i = 0; i < n; i++) {
+        int c = h[dir > 0 ? i : n - 1 - i];
+        if (!to_frame(k, st, xs, sc, secv[c])) return 0;
+        real xr = k->X[rowv[c]];
+        if (xr != *xs && !propagate(st, *xs, xr, k->kB, k->smax)) return 0;
+        residual_cov_inv(st, k, &g);
+        *chi2sum = *chi2sum + chi2_of(&g, Y[c] - st->p[0], Zc[c] - st->p[1]);
+        kf_update(st, &g, Y[c], Zc[c]);
+        *xs = xr;
+    }
+    return 1;
+}
+
+typedef struct {
+    int ok;
+    KS in, out;                   /* states at the innermost and outermost cluster */
+    real x_in, x_out;
+    int s_in, s_out;              /* frame sectors */
+    real chi2;                    /* sum of the inward pass's update chi2 */
+    real r_in, r_out;             /* transverse radius of the innermost and outermost cluster */
+} Refit;
+
+/* Refit of a cluster list h[0..n-1] (inner to outer): seed from the circle through the first,
+ * middle and last clusters (taken into the first cluster's frame), outward pass with the seed
+ * covariance, inward pass with the covariance reset to the seed's, exactly as the tracklet
+ * construction does but on the given clusters; the inward pass's last state is the result. */
+static void refit(const K *k, const real *Y, const real *Zc, const uint8_t *rowv, const int32_t *secv,
+                  const int32_t *h, int n, Refit *o)
+{
+    memset(o, 0, sizeof *o);
+    if (n < 3) return;
+    int s0 = secv[h[0]];
+    int idx[3] = {0, (n - 1) / 2, n - 1};
+    real x3[3], y3[3], z3[3];
+    for (int i = 0; i < 3; i++) {
+        int c = h[idx[i]];
+        int d = rot_steps(secv[c], s0);
+        real x = k->X[rowv[c]], yv = Y[c];
+        real cd = k->crot[d], sd = k->srot[d];
+        x3[i] = d == 0 ? x : FMA(x, cd, yv * sd);
+        y3[i] = d == 0 ? yv : FMA(yv, cd, -(x * sd));
+        z3[i] = Zc[c];
+    }
+    KS st;
+    if (!seed3(x3, y3, z3, k->kB, k->smax, st.p)) return;
+    set_diag(&st, k->cov0);
+    real xs = k->X[rowv[h[0]]];
+    int sc = s0;
+    real dummy = 0;
+    if (!refit_pass(k, Y, Zc, rowv, secv, h, n, 1, &st, &xs, &sc, &dummy)) return;
+    o->out = st;
+    o->x_out = xs;
+    o->s_out = sc;
+    set_diag(&st, k->cov0);
+    real chi2 = 0;
+    if (!refit_pass(k, Y, Zc, rowv, secv, h, n, -1, &st, &xs, &sc, &chi2)) return;
+    o->in = st;
+    o->x_in = xs;
+    o->s_in = sc;
+    o->chi2 = chi2;
+    int ci = h[0], co = h[n - 1];
+    real xi = k->X[rowv[ci]], xo = k->X[rowv[co]];
+    o->r_in = SQRT(FMA(xi, xi, Y[ci] * Y[ci]));
+    o->r_out = SQRT(FMA(xo, xo, Y[co] * Y[co]));
+    o->ok = 1;
+}
+
+/* chi2 = d^T A^-1 d for a symmetric 5x5 A (lower triangle used): Cholesky factor L (A = L L^T),
+ * then u = L^-1 d by forward substitution and chi2 = |u|^2.  0 if A is not positive definite. */
+static int chi2_5(const real A[5][5], const real d[5], real *chi2)
+{
+    real L[5][5], u[5];
+    for (int i = 0; i < 5; i++)
+        for (int j = 0; j <= i; j++) {
+            real t = A[i][j];
+            for (int m = 0; m < j; m++) t = FMA(-L[i][m], L[j][m], t);
+            if (i == j) {
+                if (!(t > 0)) return 0;
+                L[i][i] = SQRT(t);
+            } else {
+                L[i][j] = t / L[j][j];
+            }
+        }
+    real q = 0;
+    for (int i = 0; i < 5; i++) {
+        real t = d[i];
+        for (int m = 0; m < i; m++) t = FMA(-L[i][m], u[m], t);
+        u[i] = t / L[i][i];
+        q = FMA(u[i], u[i], q);
+    }
+    *chi2 = q;
+    return 1;
+}
+
+/* Compatibility of track a's outer end with track b's inner end (b continuing a outwards):
+ * radial gap in (0, mgap], q/pT within the gate, then a's outer state taken into b's frame and
+ * transported to b's innermost cluster, and chi2 of the 5-parameter difference with the summed
+ * covariances.  `ar` is a's outer state already in b's frame at x = xa. */
+static int match_chi2(const K *k, const Refit *a, const KS *ar, real xa, const Refit *b, real *chi2)
+{
+    real gap = b->r_in - a->r_out;
+    if (!(gap > 0 && gap <= k->mgap)) return 0;
+    real dq = b->in.p[4] - ar->p[4];
+    if (!(dq * dq <= k->mq2 * (ar->C[4][4] + b->in.C[4][4]))) return 0;
+    KS pr = *ar;
+    if (xa != b->x_in && !propagate(&pr, xa, b->x_in, k->kB, k->smax)) return 0;
+    real A[5][5], d[5];
+    for (int i = 0; i < 5; i++) {
+        d[i] = b->in.p[i] - pr.p[i];
+        for (int j = 0; j <= i; j++) A[i][j] = pr.C[i][j] + b->in.C[i][j];
+    }
+    if (!chi2_5(A, d, chi2)) return 0;
+    return *chi2 <= k->mchi2;
+}
+
+/* Merger over the event's sector tracks (res->trk_*); fills res->rf_* (refit of every sector
+ * track), res->mg_next and the merged tracks res->mrg_*. */
+static void merge_tracks(const K *k, const real *Y, const real *Zc, const uint8_t *rowv, const int32_t *secv,
+                         orc_result *res, int nth)
+{
+    int64_t M = res->n_tracks;
+    size_t mm = (size_t)(M > 0 ? M : 1);
+    Refit *rf = (Refit *)calloc(mm, sizeof(Refit));
+    (void)nth;
+#ifdef _OPENMP
+#pragma omp parallel for schedule(dynamic, 64) num_threads(nth > 0 ? nth : omp_get_max_threads())
+#endif
+    for (int64_t m = 0; m < M; m++)
+        refit(k, Y, Zc, rowv, secv, res->trk_hits + res->trk_first[m], res->trk_nhits[m], &rf[m]);
+    /* tracks by the sector of their innermost cluster, in track order (counting sort) */
+    int64_t sec_first[37];
+    int32_t *by_sec = (int32_t *)malloc(mm * sizeof(int32_t));
+    memset(sec_first, 0, sizeof sec_first);
+    for (int64_t m = 0; m < M; m++) sec_first[secv[res->trk_hits[res->trk_first[m]]] + 1]++;
+    for (int s = 0; s < 36; s++) sec_first[s + 1] += sec_first[s];
+    {
+        int64_t cur[36];
+        for (int s = 0; s < 36; s++) cur[s] = sec_first[s];
+        for (int64_t m = 0; m < M; m++) by_sec[cur[secv[res->trk_hits[res->trk_first[m]]]]++] = (int32_t)m;
+    }
+    /* best partner of every outer end; best partner of every inner end (ties: lower index) */
+    int32_t *best = (int32_t *)malloc(mm * sizeof(int32_t));
+    int32_t *bbest = (int32_t *)malloc(mm * sizeof(int32_t));
+    real *bchi = (real *)malloc(mm * sizeof(real));
+    real *bbchi = (real *)malloc(mm * sizeof(real));
+    for (int64_t m = 0; m < M; m++) {
+        best[m] = bbest[m] = -1;
+        bchi[m] = bbchi[m] = 0;
+    }
+    for (int64_t a = 0; a < M; a++) {
+        if (!rf[a].ok) continue;
+        int sa = rf[a].s_out, side = sa / 18, az = sa % 18;
+        int cand[3] = {(1 - side) * 18 + az, side * 18 + (az + 1) % 18, side * 18 + (az + 17) % 18};
+        for (int q = 0; q < 3; q++) {
+            int sb = cand[q];
+            KS ar = rf[a].out;
+            real xa = rf[a].x_out;
+            int sc = sa;
+            if (!to_frame(k, &ar, &xa, &sc, sb)) continue;
+            for (int64_t ib = sec_first[sb]; ib < sec_first[sb + 1]; ib++) {
+                int64_t b = by_sec[ib];
+                if (b == a || !rf[b].ok) continue;
+                real chi2;
+                if (!match_chi2(k, &rf[a], &ar, xa, &rf[b], &chi2)) continue;
+                if (best[a] < 0 || chi2 < bchi[a] || (chi2 == bchi[a] && b < best[a])) {
+                    best[a] = (int32_t)b;
+                    bchi[a] = chi2;
+                }
+                if (bbest[b] < 0 || chi2 < bbchi[b] || (chi2 == bbchi[b] && a < bbest[b])) {
+                    bbest[b] = (int32_t)a;
+                    bbchi[b] = chi2;
+                }
+            }
+        }
+    }
+    /* mutual best pairs are merged; radii increase along a chain, so chains have no cycles */
+    int32_t *prev = (int32_t *)malloc(mm * sizeof(int32_t));
+    for (int64_t m = 0; m < M; m++) prev[m] = -1;
+    for (int64_t a = 0; a < M; a++) {
+        int32_t b = best[a];
+        res->mg_next[a] = (b >= 0 && bbest[b] == a) ? b : -1;
+        if (res->mg_next[a] >= 0) prev[b] = (int32_t)a;
+    }
+    for (int64_t m = 0; m < M; m++) {
+        for (int i = 0; i < 5; i++) res->rf_par[m * 5 + i] = (double)rf[m].in.p[i];
+        int q = 0;
+        for (int i = 0; i < 5; i++)
+            for (int j = 0; j <= i; j++) res->rf_cov[m * 15 + q++] = (double)rf[m].in.C[i][j];
+        res->rf_x[m] = (double)rf[m].x_in;
+        res->rf_chi2[m] = (double)rf[m].chi2;
+        res->rf_ok[m] = rf[m].ok;
+    }
+    /* merged tracks: one per chain head, in canonical order; clusters of the chain's tracks in
+     * order, refitted over all of them */
+    int64_t Mm = 0, Hm = 0;
+    for (int64_t m = 0; m < M; m++)
+        if (prev[m] < 0) {
+            Mm++;
+            for (int64_t t = m; t >= 0; t = res->mg_next[t]) Hm += res->trk_nhits[t];
+        }
+    res->n_merged = Mm;
+    res->n_merged_hits = Hm;
+    size_t mmm = (size_t)(Mm > 0 ? Mm : 1);
+    res->mrg_first = (int32_t *)malloc(mmm * sizeof(int32_t));
+    res->mrg_nhits = (int32_t *)malloc(mmm * sizeof(int32_t));
+    res->mrg_nseg = (int32_t *)malloc(mmm * sizeof(int32_t));
+    res->mrg_head = (int32_t *)malloc(mmm * sizeof(int32_t));
+    res->mrg_hits = (int32_t *)malloc((size_t)(Hm > 0 ? Hm : 1) * sizeof(int32_t));
+    res->mrg_par = (double *)calloc(mmm * 5, sizeof(double));
+    res->mrg_cov = (double *)calloc(mmm * 15, sizeof(double));
+    res->mrg_x = (double *)calloc(mmm, sizeof(double));
+    res->mrg_chi2 = (double *)calloc(mmm, sizeof(double));
+    res->mrg_ndf = (int32_t *)calloc(mmm, sizeof(int32_t));
+    res->mrg_sector = (int32_t *)calloc(mmm, sizeof(int32_t));
+    res->mrg_ok = (int32_t *)calloc(mmm, sizeof(int32_t));
+    int64_t j = 0, h = 0;
+    for (int64_t m = 0; m < M; m++) {
+        if (prev[m] >= 0) continue;
+        res->mrg_head[j] = (int32_t)m;
+        res->mrg_first[j] = (int32_t)h;
+        int nseg = 0;
+        for (int64_t t = m; t >= 0; t = res->mg_next[t]) {
+            for (int i = 0; i < res->trk_nhits[t]; i++) res->mrg_hits[h++] = res->trk_hits[res->trk_first[t] + i];
+            nseg++;
+        }
+        res->mrg_nhits[j] = (int32_t)(h - res->mrg_first[j]);
+        res->mrg_nseg[j] = nseg;
+        j++;
+    }
+#ifdef _OPENMP
+#pragma omp parallel for schedule(dynamic, 64) num_threads(nth > 0 ? nth : omp_get_max_threads())
+#endif
+    for (int64_t i = 0; i < Mm; i++) {
+        int64_t m = res->mrg_head[i];
+        Refit r;
+        if (res->mrg_nseg[i] > 1)
+            refit(k, Y, Zc, rowv, secv, res->mrg_hits + res->mrg_first[i], res->mrg_nhits[i], &r);
+        else
+            r = rf[m];
+        if (r.ok) {
+            for (int a = 0; a < 5; a++) res->mrg_par[i * 5 + a] = (double)r.in.p[a];
+            int q = 0;
+            for (int a = 0; a < 5; a++)
+                for (int b = 0; b <= a; b++) res->mrg_cov[i * 15 + q++] = (double)r.in.C[a][b];
+            res->mrg_x[i] = (double)r.x_in;
+            res->mrg_chi2[i] = (double)r.chi2;
+            res->mrg_ndf[i] = 2 * res->mrg_nhits[i] - 5;
+            res->mrg_sector[i] = r.s_in;
+        } else {                            /* refit failed: the sector tracker's parameters */
+            for (int a = 0; a < 5; a++) res->mrg_par[i * 5 + a] = res->trk_par[m * 5 + a];
+            for (int a = 0; a < 15; a++) res->mrg_cov[i * 15 + a] = res->trk_cov[m * 15 + a];
+            res->mrg_x[i] = res->trk_x[m];
+            res->mrg_chi2[i] = res->trk_chi2[m];
+            res->mrg_ndf[i] = res->trk_ndf[m];
+            res->mrg_sector[i] = res->trk_sector[m];
+        }
+        res->mrg_ok[i] = r.ok;
+    }
+    free(rf);
+    free(by_sec);
+    free(best);
+    free(bbest);
+    free(bchi);
+    free(bbchi);
+    free(prev);
+}
+
 orc_result *SFX(orc_track_event)(const orc_config *cfg, const double *y, const double *z,
                                  const uint8_t *row, const int32_t *counts, int64_t n)
 {
@@ -977,6 +1284,29 @@ orc_result *SFX(orc_track_event)(const orc_config *cfg, const double *y, const d
     for (int s = 0; s < ns; s++)
         for (int i = 0; i < ORC_INFO_COUNT; i++) res->counters[i] += S[s].cnt[i];
 
+    /* track merger with refit */
+    {
+        size_t mm = (size_t)(M > 0 ? M : 1);
+        res->rf_par = (double *)calloc(mm * 5, sizeof(double));
+        res->rf_cov = (double *)calloc(mm * 15, sizeof(double));
+        res->rf_x = (double *)calloc(mm, sizeof(double));
+        res->rf_chi2 = (double *)calloc(mm, sizeof(double));
+        res->rf_ok = (int32_t *)calloc(mm, sizeof(int32_t));
+        res->mg_next = (int32_t *)malloc(mm * sizeof(int32_t));
+        for (size_t i = 0; i < mm; i++) res->mg_next[i] = -1;
+        if (k.merge) {
+            int32_t *secv = (int32_t *)malloc(sizeof(int32_t) * (size_t)(n > 0 ? n : 1));
+            for (int s = 0; s < ns; s++)
+                for (int64_t i = S[s].off; i < S[s].off + S[s].n; i++) secv[i] = s;
+#ifdef _OPENMP
+            merge_tracks(&k, Y, Zc, row, secv, res, nth);
+#else
+            merge_tracks(&k, Y, Zc, row, secv, res, 0);
+#endif
+            free(secv);
+        }
+    }
+
     for (int s = 0; s < ns; s++) {
         for (int r = 0; r < nr; r++) {
             free(S[s].rows[r].cstart);
@@ -1033,6 +1363,17 @@ int orc_rotate_f64(double *state, double *cov15, double x, double cos_d, double 
         for (int j = 0; j <= i; j++) cov15[q++] = s.C[i][j];
     *x_new = xn;
     return ok;
+}
+
+int orc_chi2_5_f64(const double *A15, const double *d5, double *chi2)
+{
+    double A[5][5], d[5];
+    int q = 0;
+    for (int i = 0; i < 5; i++) {
+        d[i] = d5[i];
+        for (int j = 0; j <= i; j++) A[i][j] = A[j][i] = A15[q++];
+    }
+    return chi2_5(A, d, chi2);
 }
 
 int orc_seed_f64(const double *x3, const double *y3, const double *z3, double bz, double sin_max,
