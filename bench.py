@@ -311,7 +311,7 @@ def run_ours(args):
     n_serial = min(args.steps, 40)
     starts = [torch.cuda.Event(enable_timing=True) for _ in range(n_serial)]
     ends = [torch.cuda.Event(enable_timing=True) for _ in range(n_serial)]
-    stage_ms = np.zeros(8)
+    stage_ms = np.zeros(9)
     stats_all = []
     results = []
     barrier()
@@ -365,7 +365,7 @@ def run_ours(args):
     global_line = {
         "events_per_s": n_g / (sum(g_ms) / 1e3), "ms_per_event": float(np.mean(g_ms)), "steps": n_g,
         "stages_ms": {n: round(float(v), 4) for n, v in zip(
-            ["setup", "ingest", "neighbours", "evolution", "construction", "selection", "output", "global"], g_stage)},
+            ["setup", "ingest", "neighbours", "evolution", "construction", "selection", "output", "global", "merge"], g_stage)},
         "clusters_found_per_event": float(np.mean([s_["global_found"] for s_ in g_stats])),
         "clusters_added_per_event": float(np.mean([g_stats[k]["hits"] - stats_all[k]["hits"] for k in range(n_g)])),
         "tracks_per_event": float(np.mean([s_["tracks"] for s_ in g_stats])),
@@ -406,7 +406,7 @@ def run_ours(args):
 
     if rank != 0:
         return 0
-    names = ["setup", "ingest", "neighbours", "evolution", "construction", "selection", "output", "global"]
+    names = ["setup", "ingest", "neighbours", "evolution", "construction", "selection", "output", "global", "merge"]
     mean_stage = stage_ms / n_serial
     stages = {n: round(float(v), 4) for n, v in zip(names, mean_stage)}
     peak, peak_kind = measured_peaks()

@@ -59,7 +59,8 @@ enum {
     TPC_STAGE_CONSTRUCTION = 4,/* A5 */
     TPC_STAGE_SELECTION = 5,   /* A6 */
     TPC_STAGE_OUTPUT = 6,      /* A7 */
-    TPC_STAGE_GLOBAL = 7       /* global tracking (Section 5), between A6 and A7 */
+    TPC_STAGE_GLOBAL = 7,      /* global tracking (Section 5), between A6 and A7 */
+    TPC_STAGE_MERGE = 8        /* track merger with refit, after A7 */
 };
 
 /* Detector geometry (Section 1: two volumes of 18 trapezoidal sectors, 159 pad rows).
@@ -93,6 +94,13 @@ typedef struct {
     float qpt_max;             /* low-momentum cut: |q/pT| <= qpt_max */
     int global_tracking;       /* 1: prolong every track into the neighbouring sectors (Section 5); only
                                   with 36 sectors, ignored otherwise; 0 by default */
+    int merge;                 /* 1: track merger with refit (Sections 1 and 3.3): every track is refitted
+                                  from its clusters alone and tracks continuing each other across a sector
+                                  border (azimuth neighbours, or the other z half) are merged; only with 36
+                                  sectors; 0 by default.  The result then holds the merged tracks. */
+    float merge_chi2;          /* 5-parameter chi2 gate of a merge */
+    float merge_gap;           /* largest radial gap (cm) between the merged ends */
+    float merge_qpt_nsigma;    /* q/pT gate of a merge, in combined sigmas */
 } tpc_params;
 
 /* Launch and grid choices.  None of them changes any result (every search
@@ -234,19 +242,20 @@ int tpc_last_error_detail(tpc_tracker *tr, int *event, int *sector, int *stage);
 
 /* Statistics of one call.  ms[] holds device milliseconds per stage, measured with
  * CUDA events on the call's stream when timing was enabled for the call (zeros
- * otherwise): ms[0] set-up copies and clears, ms[TPC_STAGE_INGEST .. TPC_STAGE_GLOBAL]
+ * otherwise): ms[0] set-up copies and clears, ms[TPC_STAGE_INGEST .. TPC_STAGE_MERGE]
  * the stages.  The counts are the work units the roofline figures are based on. */
 typedef struct {
-    float ms[8];
+    float ms[10];
     int kernel_launches;           /* kernels this library launched for the call */
     int64_t clusters;              /* input clusters */
     int64_t tracklets;             /* start hits = tracklets built (A4, A5) */
     int64_t row_visits;            /* A5 row visits (searches), both passes */
     int64_t candidates;            /* A5 clusters read inside the searched grid cells */
-    int64_t tracks;                /* output tracks */
+    int64_t tracks;                /* output tracks (after the merger when it runs) */
     int64_t hits;                  /* output clusters */
     int64_t global_found;          /* clusters found by the global-tracking prolongations (before claims) */
     int64_t graph_builds;          /* executable graphs the tracker instantiated up to this call (graph mode) */
+    int64_t sector_tracks;         /* tracks before the merger (= tracks when it does not run) */
 } tpc_call_stats;
 
 /* Host-side fault injection for failure tests; no GPU fault is involved.  what = 0: off;

@@ -759,6 +759,8 @@ static int prolong(Sector *S, const K *k, const real *Y, const real *Zc, int s, 
 /* lists give bitwise equal results whatever rounding the sector tracker saw)                   */
 /* ----------------------------------------------------------------------------------------- */
 
+#define ORC_MAX_CHAIN 64   /* bound on a chain walk (radii increase along a chain, so it never binds) */
+
 /* Steps of 20 degrees that take frame `from` to frame `to` (0..17; same azimuth: 0). */
 static int rot_steps(int from, int to) { return ((to % 18) - (from % 18) + 18) % 18; }
 
@@ -978,7 +980,8 @@ static void merge_tracks(const K *k, const real *Y, const real *Zc, const uint8_
     for (int64_t m = 0; m < M; m++)
         if (prev[m] < 0) {
             Mm++;
-            for (int64_t t = m; t >= 0; t = res->mg_next[t]) Hm += res->trk_nhits[t];
+            int64_t t = m;
+            for (int step = 0; step < ORC_MAX_CHAIN && t >= 0; step++, t = res->mg_next[t]) Hm += res->trk_nhits[t];
         }
     res->n_merged = Mm;
     res->n_merged_hits = Hm;
@@ -1001,7 +1004,8 @@ static void merge_tracks(const K *k, const real *Y, const real *Zc, const uint8_
         res->mrg_head[j] = (int32_t)m;
         res->mrg_first[j] = (int32_t)h;
         int nseg = 0;
-        for (int64_t t = m; t >= 0; t = res->mg_next[t]) {
+        int64_t t = m;
+        for (int step = 0; step < ORC_MAX_CHAIN && t >= 0; step++, t = res->mg_next[t]) {
             for (int i = 0; i < res->trk_nhits[t]; i++) res->mrg_hits[h++] = res->trk_hits[res->trk_first[t] + i];
             nseg++;
         }

@@ -18,7 +18,7 @@ import numpy as np
 
 from .tracker import Tracker, tpc_tuning_default
 
-STAGES = ["setup", "ingest", "neighbours", "evolution", "construction", "selection", "output", "global"]
+STAGES = ["setup", "ingest", "neighbours", "evolution", "construction", "selection", "output", "global", "merge"]
 
 
 def _as_dict(t):

@@ -95,7 +95,7 @@ struct tpc_result {
     int launches = 0;
     int64_t graph_builds = 0;            // the tracker's graph instantiations up to this call
     bool timed = false;
-    cudaEvent_t stage_ev[9] = {};
+    cudaEvent_t stage_ev[10] = {};
 };
 
 bool tpc::tracker_info(const tpc_tracker *tr, TrackerInfo *out)
@@ -153,6 +153,10 @@ extern "C" void tpc_params_default(tpc_params *p)
     p->min_clusters = 30;       // Section 5
     p->qpt_max = 20.0f;
     p->global_tracking = 0;
+    p->merge = 0;
+    p->merge_chi2 = 25.0f;
+    p->merge_gap = 40.0f;
+    p->merge_qpt_nsigma = 5.0f;
 }
 
 extern "C" void tpc_tuning_default(tpc_tuning *t)
@@ -216,6 +220,16 @@ static void fill_const(tpc_tracker *tr, float bz)
     c.global = (p.global_tracking && tr->n_sectors == 36) ? 1 : 0;
     c.c20 = (float)std::cos(20.0 * 3.14159265358979323846 / 180.0);
     c.s20 = (float)std::sin(20.0 * 3.14159265358979323846 / 180.0);
+    c.merge = (p.merge && tr->n_sectors == 36) ? 1 : 0;
+    for (int d = 0; d < 18; d++) {
+        const int deg = d <= 9 ? 20 * d : 20 * (d - 18);     // -160 .. 180
+        const double a = (double)(deg < 0 ? -deg : deg) * 3.14159265358979323846 / 180.0;
+        c.crot[d] = (float)std::cos(a);
+        c.srot[d] = deg < 0 ? -(float)std::sin(a) : (float)std::sin(a);
+    }
+    c.mchi2 = p.merge_chi2;
+    c.mgap = p.merge_gap;
+    c.mq2 = (float)((double)p.merge_qpt_nsigma * (double)p.merge_qpt_nsigma);
 }
 
 extern "C" int tpc_tracker_create(const tpc_geometry *g, float bz, const tpc_params *params, size_t budget,
@@ -344,6 +358,47 @@ static size_t carve(tpc_tracker *tr, const WsSizes &s, Alloc &a)
         w.gpool = w.g_off = w.g_n = w.g_own = w.g_sec = nullptr;
         w.gpool_cap = 0;
     }
+    if (tr->dc.merge) {
+        const int64_t S = s.R / tr->n_rows + 2;
+        w.in_sec = a.take<int32_t>(s.P);
+        w.st.par = a.take<float>(5 * s.T);
+        w.st.cov = a.take<float>(15 * s.T);
+        w.st.x = a.take<float>(s.T);
+        w.st.alpha = a.take<float>(s.T);
+        w.st.chi2 = a.take<float>(s.T);
+        w.st.ndf = a.take<int32_t>(s.T);
+        w.st.nhits = a.take<int32_t>(s.T);
+        w.st.first = a.take<int32_t>(s.T);
+        w.st.sector = a.take<int32_t>(s.T);
+        w.st.event = a.take<int32_t>(s.T);
+        w.st.hits = a.take<int32_t>(s.P);
+        w.rf_ok = a.take<int32_t>(s.T);
+        w.rf_sin = a.take<int32_t>(s.T);
+        w.rf_sout = a.take<int32_t>(s.T);
+        w.rf_P = a.take<float>(5 * s.T);
+        w.rf_C = a.take<float>(15 * s.T);
+        w.rf_oP = a.take<float>(5 * s.T);
+        w.rf_oC = a.take<float>(15 * s.T);
+        w.rf_xin = a.take<float>(s.T);
+        w.rf_xout = a.take<float>(s.T);
+        w.rf_rin = a.take<float>(s.T);
+        w.rf_rout = a.take<float>(s.T);
+        w.rf_chi2 = a.take<float>(s.T);
+        w.mg_sec_cnt = a.take<int32_t>(S);
+        w.mg_sec_first = a.take<int32_t>(S);
+        w.mg_sec_cur = a.take<int32_t>(S);
+        w.mg_by_sec = a.take<int32_t>(s.T);
+        w.mg_best = a.take<int32_t>(s.T);
+        w.mg_next = a.take<int32_t>(s.T);
+        w.mg_prev = a.take<int32_t>(s.T);
+        w.mg_head = a.take<int32_t>(s.T);
+        w.mg_cnt = a.take<int32_t>(s.T);
+        w.mg_idx = a.take<int32_t>(s.T);
+        w.mg_first = a.take<int32_t>(s.T);
+        w.mg_bkey = a.take<unsigned long long>(s.T);
+        w.mg_nseg = a.take<int32_t>(s.T);
+        w.mg_headof = a.take<int32_t>(s.T);
+    }
     w.bits = a.take<uint32_t>(s.W);
     w.word_off = a.take<int32_t>(s.W);
     w.rank_trk = a.take<int32_t>(s.T);
@@ -451,7 +506,7 @@ static int run(tpc_tracker *tr, const float *y, const float *z, const uint8_t *r
         tr->free_results.pop_back();
         cudaEvent_t keep_done = res->done;
         int32_t *keep_counts = res->h_counts;
-        cudaEvent_t keep_ev[9];
+        cudaEvent_t keep_ev[10];
         memcpy(keep_ev, res->stage_ev, sizeof keep_ev);
         *res = tpc_result();
         res->done = keep_done;
@@ -614,8 +669,10 @@ static int run(tpc_tracker *tr, const float *y, const float *z, const uint8_t *r
     mark(6);
     if (tr->dc.global) launches += launch_global(tr->dc, w, s_off, lc, ls);
     mark(8);
-    launches += launch_output(tr->dc, w, res->out, n_total, lc, ls);
+    launches += launch_output(tr->dc, w, tr->dc.merge ? w.st : res->out, n_total, lc, ls);
     mark(7);
+    if (tr->dc.merge) launches += launch_merge(tr->dc, w, res->out, y, z, row, R, lc, ls);
+    mark(9);
     chk(cudaGetLastError());
     if (graph) {
         cudaGraph_t g = nullptr;
@@ -881,6 +938,7 @@ extern "C" int tpc_result_stats(tpc_result *r, tpc_call_stats *st)
         for (int i = 0; i < 6; i++) TPC_CUDA(cudaEventElapsedTime(&st->ms[i], r->stage_ev[i], r->stage_ev[i + 1]));
         TPC_CUDA(cudaEventElapsedTime(&st->ms[TPC_STAGE_GLOBAL], r->stage_ev[6], r->stage_ev[8]));
         TPC_CUDA(cudaEventElapsedTime(&st->ms[TPC_STAGE_OUTPUT], r->stage_ev[8], r->stage_ev[7]));
+        TPC_CUDA(cudaEventElapsedTime(&st->ms[TPC_STAGE_MERGE], r->stage_ev[7], r->stage_ev[9]));
     }
     st->kernel_launches = r->launches;
     st->clusters = r->n_clusters;
@@ -891,6 +949,7 @@ extern "C" int tpc_result_stats(tpc_result *r, tpc_call_stats *st)
     st->hits = r->h_counts[CNT_HITS];
     st->global_found = r->h_counts[CNT_GPOOL];
     st->graph_builds = r->graph_builds;
+    st->sector_tracks = r->tr->dc.merge ? r->h_counts[CNT_STRACKS] : r->h_counts[CNT_TRACKS];
     return TPC_OK;
 }
 

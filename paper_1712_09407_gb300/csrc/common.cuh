@@ -29,6 +29,8 @@ enum {
     CNT_SW_CHUNKS = 6,  // chunks of the sector-sweep constructor
     CNT_GPOOL = 7,      // global tracking: entries appended to the prolongation pool
     CNT_GLIST = 8,      // global tracking: prolongations of the call (2 per tracklet)
+    CNT_STRACKS = 9,    // merger: sector tracks (CNT_TRACKS then counts the merged tracks)
+    CNT_SHITS = 10,     // merger: clusters of the sector tracks
     CNT_COUNT = 12
 };
 
@@ -57,6 +59,14 @@ struct DevConst {
     int inject;         // host-side test hook (0 = off): 1 makes one staging wait of the neighbours finder expire
     int global;         // global tracking on (Section 5)
     float c20, s20;     // cos, sin of the 20 degree sector pitch
+    int merge;          // track merger with refit
+    float crot[18], srot[18];   // cos, sin of d * 20 degrees (d = 0..17, read as -160..180)
+    float mchi2, mgap, mq2;     // merger gates: chi2, radial gap, (q/pT sigmas)^2
+};
+
+struct OutBuffers {
+    float *par, *cov, *x, *alpha, *chi2;
+    int32_t *ndf, *nhits, *first, *sector, *event, *hits;
 };
 
 // Per row unit metadata (host-computed): input offset, count, sorted offset, cell offset.
@@ -98,6 +108,17 @@ struct Workspace {
     float *g_chi;          // [2 * tcap]
     float *g_par, *g_cov, *g_x;         // inward prolongation's last state [5|15|1][tcap]
     int32_t *g_sec;        // [tcap] sector (within the event) of that state
+    // track merger
+    int32_t *in_sec;       // [input clusters] sector (index within the call)
+    OutBuffers st;         // sector tracks (A7 output) when the merger runs after them
+    int32_t *rf_ok, *rf_sin, *rf_sout;  // [tcap] refit of every sector track
+    float *rf_P, *rf_C, *rf_oP, *rf_oC; // [5|15][tcap] states at the innermost / outermost cluster
+    float *rf_xin, *rf_xout, *rf_rin, *rf_rout, *rf_chi2;
+    int32_t *mg_sec_cnt, *mg_sec_first, *mg_sec_cur;   // [sectors + 1] tracks per inner sector
+    int32_t *mg_by_sec;    // [tcap] tracks grouped by inner sector
+    int32_t *mg_best, *mg_next, *mg_prev, *mg_head, *mg_cnt, *mg_idx, *mg_first;   // [tcap]
+    unsigned long long *mg_bkey;        // [tcap] best outer end for every inner end
+    int32_t *mg_nseg, *mg_headof;       // [tcap] per merged track
     // output ordering
     uint32_t *bits;        // bitmap over input indices of innermost clusters
     int32_t *word_off;     // exclusive prefix of popcounts
@@ -125,11 +146,6 @@ __device__ __forceinline__ uint64_t global_ns()
     return t;
 }
 constexpr uint64_t kWaitNs = 1000000000ull;   // every device wait gives up after 1 s
-
-struct OutBuffers {
-    float *par, *cov, *x, *alpha, *chi2;
-    int32_t *ndf, *nhits, *first, *sector, *event, *hits;
-};
 
 // --------------------------------------------------------------------------------------------
 // device helpers
@@ -217,6 +233,8 @@ int launch_select(const DevConst &c, const Workspace &w, int64_t n_input, const 
 int launch_output(const DevConst &c, const Workspace &w, const OutBuffers &o, int64_t n_input,
                    const LaunchCfg &lc, cudaStream_t s);
 int launch_global(const DevConst &c, const Workspace &w, int64_t n_slots, const LaunchCfg &lc, cudaStream_t s);
+int launch_merge(const DevConst &c, const Workspace &w, const OutBuffers &o, const float *y, const float *z,
+                 const uint8_t *row, int64_t R, const LaunchCfg &lc, cudaStream_t s);
 // Exclusive scan of min(n, *n_dev) int32 values (n_dev may be null); total to *total_out if given.
 // partials needs n / 4096 + 64 ints.  Returns the kernels launched.
 int launch_scan_i32(const int32_t *in, int32_t *out, int64_t n, const int32_t *n_dev, int32_t *partials,

@@ -21,7 +21,8 @@ _lock = threading.Lock()
 _lib = None
 
 TPC_OK, TPC_ERR_INVALID_ARG, TPC_ERR_CAPACITY, TPC_ERR_BUDGET, TPC_ERR_TIMEOUT, TPC_ERR_CUDA, TPC_ERR_STATE = range(7)
-STAGES = {0: "none", 1: "ingest", 2: "neighbours", 3: "evolution", 4: "construction", 5: "selection", 6: "output"}
+STAGES = {0: "none", 1: "ingest", 2: "neighbours", 3: "evolution", 4: "construction", 5: "selection", 6: "output",
+          7: "global", 8: "merge"}
 
 c_int, c_float, c_int64, c_void_p = ctypes.c_int, ctypes.c_float, ctypes.c_int64, ctypes.c_void_p
 P = ctypes.POINTER
@@ -37,7 +38,8 @@ class tpc_params(ctypes.Structure):
                 ("nb_gate", c_float), ("min_chain", c_int), ("seed_cov", c_float * 5),
                 ("win_nsigma", c_float), ("chi2_max", c_float), ("max_miss", c_int),
                 ("edge_margin", c_float), ("sin_max", c_float), ("alpha", c_float), ("beta", c_float),
-                ("min_clusters", c_int), ("qpt_max", c_float), ("global_tracking", c_int)]
+                ("min_clusters", c_int), ("qpt_max", c_float), ("global_tracking", c_int), ("merge", c_int),
+                ("merge_chi2", c_float), ("merge_gap", c_float), ("merge_qpt_nsigma", c_float)]
 
 
 class tpc_tuning(ctypes.Structure):
@@ -61,9 +63,9 @@ class tpc_debug_view(ctypes.Structure):
 
 
 class tpc_call_stats(ctypes.Structure):
-    _fields_ = [("ms", c_float * 8), ("kernel_launches", c_int), ("clusters", c_int64), ("tracklets", c_int64),
+    _fields_ = [("ms", c_float * 10), ("kernel_launches", c_int), ("clusters", c_int64), ("tracklets", c_int64),
                 ("row_visits", c_int64), ("candidates", c_int64), ("tracks", c_int64), ("hits", c_int64),
-                ("global_found", c_int64), ("graph_builds", c_int64)]
+                ("global_found", c_int64), ("graph_builds", c_int64), ("sector_tracks", c_int64)]
 
 
 EXPORTS = {
@@ -252,10 +254,11 @@ def tpc_tracker_set_timing(tr, enable=True):
 def tpc_result_stats(res) -> dict:
     st = tpc_call_stats()
     _check(lib().tpc_result_stats(res, ctypes.byref(st)), "tpc_result_stats")
-    # ms: set-up, ingest, neighbours, evolution, construction, selection, output, global tracking
-    return dict(ms=list(st.ms), kernel_launches=st.kernel_launches, clusters=st.clusters,
+    # ms: set-up, ingest, neighbours, evolution, construction, selection, output, global tracking, merger
+    return dict(ms=list(st.ms)[:9], kernel_launches=st.kernel_launches, clusters=st.clusters,
                 tracklets=st.tracklets, row_visits=st.row_visits, candidates=st.candidates, tracks=st.tracks,
-                hits=st.hits, global_found=st.global_found, graph_builds=st.graph_builds)
+                hits=st.hits, global_found=st.global_found, graph_builds=st.graph_builds,
+                sector_tracks=st.sector_tracks)
 
 
 def tpc_find_links_noalloc(tr, y, z, row, counts, up, dn, status=None, stream=None, n=None):
@@ -365,10 +368,13 @@ class Tracker:
     """A tracker on the current CUDA device for one geometry."""
 
     def __init__(self, row_x, tan_half=0.17632698070846498, z_max=250.0, n_sectors=36, bz=0.5, params=None,
-                 budget=0, tuning=None, global_tracking=None):
-        if global_tracking is not None:
+                 budget=0, tuning=None, global_tracking=None, merge=None):
+        if global_tracking is not None or merge is not None:
             params = params if params is not None else tpc_params_default()
-            params.global_tracking = int(bool(global_tracking))
+            if global_tracking is not None:
+                params.global_tracking = int(bool(global_tracking))
+            if merge is not None:
+                params.merge = int(bool(merge))
         self.row_x = np.asarray(row_x, dtype=np.float32)
         self.n_rows = int(self.row_x.shape[0])
         self.n_sectors = int(n_sectors)
