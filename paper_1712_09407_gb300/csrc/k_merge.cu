@@ -235,14 +235,19 @@ __global__ void __launch_bounds__(kMergeBlock) k_mg_scatter(const Workspace w)
         if (w.rf_ok[m]) w.mg_by_sec[atomicAdd(&w.mg_sec_cur[w.rf_sin[m]], 1)] = m;
 }
 
-// Best partner of every outer end; best partner of every inner end by atomicMin.
+// Best partner of every outer end; best partner of every inner end by atomicMin.  One warp per
+// outer end: the lanes sweep the candidate sectors' lists 32 tracks at a time (coalesced index
+// loads, the radial-gap gate first), the passing lanes run the transport and the chi2, and the
+// warp's best is the minimum of (chi2 bits, track) over its lanes; chi2 >= 0, so the bits order
+// like the values and equal chi2 go to the lower track, as in a sequential scan.
 __global__ void __launch_bounds__(kMergeBlock) k_mg_match(const DevConst c, const Workspace w)
 {
     const int M = w.counters[CNT_TRACKS];
     const int64_t T = w.tcap;
-    for (int a = blockIdx.x * blockDim.x + threadIdx.x; a < M; a += gridDim.x * blockDim.x) {
-        int best = -1;
-        float bchi = 0.0f;
+    const int lane = threadIdx.x & 31;
+    const int nwarps = (gridDim.x * blockDim.x) >> 5;
+    for (int a = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; a < M; a += nwarps) {
+        unsigned long long best = ~0ull;
         if (w.rf_ok[a]) {
             const int sa = w.rf_sout[a];
             const int ev = sa / 36, side = (sa % 36) / 18, az = sa % 18;
@@ -256,9 +261,10 @@ __global__ void __launch_bounds__(kMergeBlock) k_mg_match(const DevConst c, cons
                 kf_load(w.rf_oP, w.rf_oC, T, a, ar);
                 float xa = w.rf_xout[a];
                 int sc = sa;
-                if (!to_frame(c, ar, xa, sc, sb)) continue;
-                for (int ib = b0; ib < b1; ib++) {
-                    const int b = w.mg_by_sec[ib];
+                if (!to_frame(c, ar, xa, sc, sb)) continue;       // the same for every lane
+                for (int i0 = b0; i0 < b1; i0 += 32) {
+                    const int ib = i0 + lane;
+                    const int b = ib < b1 ? w.mg_by_sec[ib] : a;
                     if (b == a) continue;
                     const float gap = w.rf_rin[b] - r_out;
                     if (!(gap > 0.0f && gap <= c.mgap)) continue;
@@ -282,15 +288,18 @@ __global__ void __launch_bounds__(kMergeBlock) k_mg_match(const DevConst c, cons
                     d[4] = bs.p4 - pr.p4;
                     float chi2;
                     if (!chi2_5(A, d, chi2) || !(chi2 <= c.mchi2)) continue;
-                    if (best < 0 || chi2 < bchi || (chi2 == bchi && b < best)) {
-                        best = b;
-                        bchi = chi2;
-                    }
+                    const unsigned long long key = ((unsigned long long)__float_as_uint(chi2) << 32) | (unsigned)b;
+                    if (key < best) best = key;
                     atomicMin(&w.mg_bkey[b], ((unsigned long long)__float_as_uint(chi2) << 32) | (unsigned)a);
                 }
             }
         }
-        w.mg_best[a] = best;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            const unsigned long long other = __shfl_xor_sync(kFull, best, o);
+            if (other < best) best = other;
+        }
+        if (lane == 0) w.mg_best[a] = best == ~0ull ? -1 : (int)(best & 0xffffffffull);
     }
 }
 
@@ -417,7 +426,7 @@ int launch_merge(const DevConst &c, const Workspace &w, const OutBuffers &o, con
     launches += launch_scan_i32(w.mg_sec_cnt, w.mg_sec_first, S + 1, nullptr, w.scan_tmp, nullptr, s);
     cudaMemcpyAsync(w.mg_sec_cur, w.mg_sec_first, (size_t)(S + 1) * sizeof(int32_t), cudaMemcpyDeviceToDevice, s);
     k_mg_scatter<<<grid, kMergeBlock, 0, s>>>(w);
-    k_mg_match<<<lc.num_sms * 16, kMergeBlock, 0, s>>>(c, w);
+    k_mg_match<<<lc.num_sms * 16, kMergeBlock, 0, s>>>(c, w);       // one warp per track
     k_mg_link<<<grid, 256, 0, s>>>(w);
     k_mg_heads<<<grid, 256, 0, s>>>(w);
     launches += 4;
