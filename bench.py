@@ -338,6 +338,34 @@ def run_ours(args):
         t.set_timing(False)
 
     # ---- global tracking (Section 5) on the same events, one at a time, L2 flushed (untimed)
+    def extra_pass(**flags):
+        """The same events one at a time with global tracking and/or the merger on."""
+        xtr = Tracker.for_geometry(ev.geometry, **flags)
+        xtr.reserve(max(p[4] for p in pool), 1)
+        n_x = min(args.steps, 20)
+        x_ms, x_stats = [], []
+        with torch.cuda.stream(stream):
+            for k in range(args.warmup):
+                d = dev[k % len(dev)]
+                r = xtr.track(d[0], d[1], d[2], d[3], stream=stream)
+                r.sync()
+                r.release()
+            xtr.set_timing(True)
+            for k in range(n_x):
+                d = dev[k % len(dev)]
+                flush.fill_(float(k))
+                a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                a.record(stream)
+                r = xtr.track(d[0], d[1], d[2], d[3], stream=stream)
+                b.record(stream)
+                r.sync()
+                x_stats.append(r.stats())
+                r.release()
+                x_ms.append(a.elapsed_time(b))
+        xtr.close()
+        st_ms = np.mean([np.array(s_["ms"]) for s_ in x_stats], axis=0)
+        return n_x, x_ms, x_stats, st_ms
+
     gtr = Tracker.for_geometry(ev.geometry, global_tracking=True)
     gtr.reserve(max(p[4] for p in pool), 1)
     n_g = min(args.steps, 20)
@@ -369,6 +397,16 @@ def run_ours(args):
         "clusters_found_per_event": float(np.mean([s_["global_found"] for s_ in g_stats])),
         "clusters_added_per_event": float(np.mean([g_stats[k]["hits"] - stats_all[k]["hits"] for k in range(n_g)])),
         "tracks_per_event": float(np.mean([s_["tracks"] for s_ in g_stats])),
+        "l2": "flushed before every event (512 MB write, untimed)"}
+    n_m, m_ms, m_stats, m_stage = extra_pass(global_tracking=True, merge=True)
+    merge_line = {
+        "what": "global tracking + track merger with refit",
+        "events_per_s": n_m / (sum(m_ms) / 1e3), "ms_per_event": float(np.mean(m_ms)), "steps": n_m,
+        "stages_ms": {n: round(float(v), 4) for n, v in zip(
+            ["setup", "ingest", "neighbours", "evolution", "construction", "selection", "output", "global", "merge"],
+            m_stage)},
+        "sector_tracks_per_event": float(np.mean([s_["sector_tracks"] for s_ in m_stats])),
+        "merged_tracks_per_event": float(np.mean([s_["tracks"] for s_ in m_stats])),
         "l2": "flushed before every event (512 MB write, untimed)"}
 
     # ---- end to end through the host-buffer entry point
@@ -430,6 +468,7 @@ def run_ours(args):
                        "parallelism": "replicas" if world > 1 else "single GPU"},
             "clusters_per_s": value * n_mean, "tracks_per_event": int(np.mean(tracks)),
             "one_event_at_a_time": serial, "stages_ms": stages, "global_tracking": global_line,
+            "global_tracking_and_merger": merge_line,
             "gpu_launches": launches, "e2e": e2e, "roofline": roof, "clocks": clk,
             "wall_s_timed_region": wall}
     if world == 1 and not args.no_cpu_baseline:
