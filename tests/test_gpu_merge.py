@@ -99,3 +99,66 @@ def test_merged_batch_equals_one_at_a_time():
         off_t += M
         off_h += H
         off_in += ev.n
+
+
+# ---------------------------------------------------------------------------------------------
+# edge cases of the optional stages
+# ---------------------------------------------------------------------------------------------
+@pytest.mark.parametrize("flags", [dict(global_tracking=True), dict(merge=True), dict(global_tracking=True, merge=True)])
+def test_optional_stages_on_empty_and_noise_only_events(flags):
+    geo = eventgen.Geometry()
+    tr = Tracker.for_geometry(geo, **flags)
+    e = torch.zeros(0, device="cuda")
+    r = tr.track(e, e, torch.zeros(0, dtype=torch.uint8, device="cuda"), np.zeros(36 * 159, np.int32))
+    assert r.sync() == (0, 0)
+    r.release()
+    rng = np.random.default_rng(1)
+    counts = rng.integers(0, 4, 36 * 159).astype(np.int32)         # sparse noise, ragged rows
+    n = int(counts.sum())
+    row = np.repeat(np.tile(np.arange(159), 36), counts).astype(np.uint8)
+    half = geo.row_x[row] * geo.tan_half
+    y = (rng.uniform(-1, 1, n) * half).astype(np.float32)
+    z = rng.uniform(-250, 250, n).astype(np.float32)
+    sec = np.repeat(np.repeat(np.arange(36), 159), counts)
+    z = np.where(sec < 18, np.abs(z), -np.abs(z)).astype(np.float32)
+    r = tr.track(*(torch.from_numpy(a).cuda() for a in (y, z, row)), counts)
+    M, H = r.sync()
+    out = r.to_numpy()
+    r.release()
+    ref = oracle.track_event(oracle.config_for(geo, **flags), y, z, row, counts, precision=32)
+    assert M == (ref.info["n_merged"] if flags.get("merge") else ref.info["n_tracks"])
+    tr.close()
+
+
+def test_flags_are_ignored_on_the_single_sector_geometry():
+    """Global tracking and the merger need the 36-sector geometry; with one sector they are off."""
+    ev = eventgen.config_event(0)
+    plain = Tracker.for_geometry(ev.geometry)
+    both = Tracker.for_geometry(ev.geometry, global_tracking=True, merge=True)
+    d = tuple(torch.from_numpy(a).cuda() for a in (ev.y, ev.z, ev.row))
+    ra, rb = plain.track(*d, ev.counts), both.track(*d, ev.counts)
+    a, b = ra.to_numpy(), rb.to_numpy()
+    ra.release()
+    rb.release()
+    for k in a:
+        assert np.array_equal(a[k], b[k]), k
+    plain.close()
+    both.close()
+
+
+def test_merger_with_a_small_tracklet_capacity_reports_capacity():
+    """A tracklet pool too small for the event fails the call with TPC_ERR_CAPACITY, merger or not."""
+    from paper_1712_09407_gb300.tracker import TrackerError, TPC_ERR_CAPACITY
+    ev = eventgen.config_event(1)
+    tr = Tracker.for_geometry(ev.geometry, global_tracking=True, merge=True)
+    tr.set_tuning(dict(tracklet_capacity=100))
+    r = tr.track(*(torch.from_numpy(a).cuda() for a in (ev.y, ev.z, ev.row)), ev.counts)
+    with pytest.raises(TrackerError) as e:
+        r.sync()
+    assert e.value.status == TPC_ERR_CAPACITY
+    r.release()
+    tr.set_tuning(dict(tracklet_capacity=0))
+    r = tr.track(*(torch.from_numpy(a).cuda() for a in (ev.y, ev.z, ev.row)), ev.counts)
+    r.sync()
+    r.release()
+    tr.close()
