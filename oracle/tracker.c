@@ -267,7 +267,8 @@ static int propagate(KS *s, real x0, real x1, real kB, real smax)
     real c1 = SQRT(FMA(-s1, s1, (real)1));
     real A = s0 + s1;
     real B = c0 + c1;
-    real tq = A / B;                          /* slope of the chord */
+    real iB = (real)1 / B;
+    real tq = A * iB;                         /* slope of the chord */
     real dy = dx * tq;
     real L = SQRT(FMA(dx, dx, dy * dy));      /* chord, signed like dx */
     if (dx < 0) L = -L;
@@ -279,14 +280,15 @@ static int propagate(KS *s, real x0, real x1, real kB, real smax)
     real F[5][5];
     memset(F, 0, sizeof F);
     for (int i = 0; i < 5; i++) F[i][i] = 1;
-    real BB = B * B;
-    F[0][2] = dx * FMA(A, s0 / c0 + s1 / c1, (real)2 * B) / BB;       /* d y1 / d sinphi0 */
-    F[0][4] = dx * (kB * dx) * FMA(A, s1 / c1, B) / BB;               /* d y1 / d q/pT */
+    /* one reciprocal of (c0 + c1) serves the chord slope and both denominators (c0 + c1)^2 */
+    real iBB = iB * iB;
+    F[0][2] = dx * FMA(A, s0 / c0 + s1 / c1, (real)2 * B) * iBB;      /* d y1 / d sinphi0 */
+    F[0][4] = dx * (kB * dx) * FMA(A, s1 / c1, B) * iBB;              /* d y1 / d q/pT */
     F[2][4] = kB * dx;                                               /* d sinphi1 / d q/pT */
-    real g = (L != 0) ? ((real)1 / SQRT(FMA(-u, u, (real)1))) * (dy / L) : (real)0; /* dS/dL * dL/ddy */
+    real g = (L != 0) ? dy / (L * SQRT(FMA(-u, u, (real)1))) : (real)0;   /* dS/dL * dL/ddy */
     F[1][2] = tl * (g * F[0][2]);                                    /* d z1 / d sinphi0 */
     F[1][3] = dS;                                                    /* d z1 / d tanl */
-    F[1][4] = tl * FMA(g, F[0][4], (((cur * L) * (L * L)) / (real)12) * kB); /* d z1 / d q/pT */
+    F[1][4] = tl * FMA(g, F[0][4], (((cur * L) * (L * L)) * (real)(1.0 / 12.0)) * kB); /* d z1 / d q/pT */
 
     s->p[0] = s->p[0] + dy;
     s->p[1] = FMA(tl, dS, s->p[1]);           /* z += tan(lambda) * arc length */

@@ -53,7 +53,8 @@ __device__ __forceinline__ bool propagate(KF &s, float dx, const DevConst &c)
     const float c1 = sqrtf(__fmaf_rn(-s1, s1, 1.0f));
     const float A = s0 + s1;
     const float B = c0 + c1;
-    const float tq = A / B;
+    const float iB = 1.0f / B;
+    const float tq = A * iB;
     const float dy = dx * tq;
     float L = sqrtf(__fmaf_rn(dx, dx, dy * dy));
     if (dx < 0.0f) L = -L;
@@ -61,15 +62,15 @@ __device__ __forceinline__ bool propagate(KF &s, float dx, const DevConst &c)
     const float ratio = asin_ratio(u);
     const float dS = L * ratio;
     const float tl = s.p3;
-    const float BB = B * B;
+    const float iBB = iB * iB;       // one reciprocal of (c0 + c1) for the slope and both denominators
     const float s1c1 = s1 / c1;
-    const float F02 = dx * __fmaf_rn(A, s0 / c0 + s1c1, 2.0f * B) / BB;
-    const float F04 = dx * (c.kB * dx) * __fmaf_rn(A, s1c1, B) / BB;
+    const float F02 = dx * __fmaf_rn(A, s0 / c0 + s1c1, 2.0f * B) * iBB;
+    const float F04 = dx * (c.kB * dx) * __fmaf_rn(A, s1c1, B) * iBB;
     const float F24 = c.kB * dx;
-    const float g = (L != 0.0f) ? (1.0f / sqrtf(__fmaf_rn(-u, u, 1.0f))) * (dy / L) : 0.0f;
+    const float g = (L != 0.0f) ? dy / (L * sqrtf(__fmaf_rn(-u, u, 1.0f))) : 0.0f;
     const float F12 = tl * (g * F02);
     const float F13 = dS;
-    const float F14 = tl * __fmaf_rn(g, F04, (((cur * L) * (L * L)) / 12.0f) * c.kB);
+    const float F14 = tl * __fmaf_rn(g, F04, (((cur * L) * (L * L)) * 0.0833333358f) * c.kB);   // 1/12 rounded to float
 
     s.p0 = s.p0 + dy;
     s.p1 = __fmaf_rn(tl, dS, s.p1);
