@@ -336,6 +336,64 @@ typedef struct {
 /* Fill *v from the tracker's last call (synchronises the device first). */
 int tpc_tracker_debug_view(tpc_tracker *tr, tpc_debug_view *v);
 
+/* ---------------------------------------------------------------------------------------
+ * Serving loop with continuous batching (the HLT requirement of the abstract: more than 200
+ * central events per second; it replaces the paper's CPU/GPU pipeline of Section 2).
+ *
+ * A server owns `lanes` trackers, each with its own stream, device input buffers and workspace
+ * reserved for lane_clusters clusters and max_batch events.  Events are submitted from any
+ * thread; a server thread forms a batch whenever a lane is free (up to max_batch events that
+ * fit the lane), copies the events' clusters from the caller's buffers, tracks the batch with
+ * one tpc_track_batch call, copies the result back and splits it per event.  Results are the
+ * same as for the event tracked alone.  The paper has no counterpart of this interface.
+ * --------------------------------------------------------------------------------------- */
+typedef struct tpc_server tpc_server;
+
+typedef struct {
+    int lanes;                 /* trackers working concurrently (>= 1) */
+    int max_batch;             /* events per batch (>= 1) */
+    int64_t lane_clusters;     /* clusters reserved per lane; larger events are refused */
+    size_t hbm_budget;         /* device bytes for all lanes together (0: no limit) */
+} tpc_server_config;
+
+/* One finished event.  Host pointers owned by the server, valid until tpc_server_release.
+ * Tracks in canonical order; hits are indices into the event's own input arrays. */
+typedef struct {
+    int status;                /* TPC_OK, or the error of this event (its batch was retried alone) */
+    int64_t n_tracks, n_hits;
+    const float *par, *cov, *x_ref, *alpha, *chi2;
+    const int32_t *ndf, *nhits, *first, *sector, *hits;
+    int64_t t_submit_ns, t_launch_ns, t_done_ns;   /* tpc_server_now_ns clock */
+    int batch_size;            /* events in the batch that carried it */
+} tpc_server_result;
+
+/* Create a server on the current device.  params: NULL for the defaults.  Returns
+ * TPC_ERR_BUDGET if a lane's buffers do not fit hbm_budget / lanes. */
+int tpc_server_create(const tpc_geometry *geometry, float bz_tesla, const tpc_params *params,
+                      const tpc_server_config *config, tpc_server **out);
+
+/* Queue one event: y, z, row are HOST arrays of n clusters (page-locked memory makes the copy
+ * asynchronous) that must stay valid until the event is reported done; counts is a host array
+ * of n_sectors * n_rows entries (copied).  *id receives the event's id.  Errors:
+ * TPC_ERR_BUDGET if n > lane_clusters, TPC_ERR_INVALID_ARG if the counts do not sum to n. */
+int tpc_server_submit(tpc_server *server, const float *y, const float *z, const uint8_t *row,
+                      const int32_t *counts, int64_t n, int64_t *id);
+
+/* Ids of events finished since the last call (at most max_ids; *n_done receives the count). */
+int tpc_server_poll(tpc_server *server, int64_t *ids, int max_ids, int *n_done);
+
+/* Result of a finished event (TPC_ERR_STATE if it is not finished yet). */
+int tpc_server_get(tpc_server *server, int64_t id, tpc_server_result *out);
+
+/* Free a finished event's result. */
+int tpc_server_release(tpc_server *server, int64_t id);
+
+/* The server's steady clock in nanoseconds. */
+int64_t tpc_server_now_ns(void);
+
+/* Finish the queued events, then free everything. */
+void tpc_server_destroy(tpc_server *server);
+
 #ifdef __cplusplus
 }
 #endif

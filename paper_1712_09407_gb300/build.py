@@ -14,7 +14,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libtpcca.so")
-SOURCES = ["api.cu", "k_links.cu", "k_construct.cu", "k_sweep.cu", "k_select.cu", "k_global.cu", "k_merge.cu", "noalloc.cu"]
+SOURCES = ["api.cu", "k_links.cu", "k_construct.cu", "k_sweep.cu", "k_select.cu", "k_global.cu", "k_merge.cu", "noalloc.cu", "server.cu"]
 HEADERS = [os.path.join(CSRC, "common.cuh"), os.path.join(CSRC, "kf.cuh"), os.path.join(os.path.dirname(HERE), "include", "tpcca.h")]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-fmad=false", "-prec-div=true", "-prec-sqrt=true",

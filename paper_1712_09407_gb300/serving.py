@@ -28,7 +28,9 @@ import time
 
 import numpy as np
 
-from .tracker import Tracker, TrackerError, tpc_result_copy_to_host
+from .tracker import (Tracker, TrackerError, server_result_arrays, tpc_result_copy_to_host, tpc_server_create,
+                      tpc_server_destroy, tpc_server_get, tpc_server_now_ns, tpc_server_poll, tpc_server_release,
+                      tpc_server_submit)
 
 # device bytes per reserved cluster: workspace (about 230 B), result (about 32 B), input (9 B)
 BYTES_PER_CLUSTER = 280
@@ -48,6 +50,10 @@ class Request:
     status: str = "pending"
     result: dict | None = None
     batch_size: int = 0
+    arrival_ns: int = 0            # native server: scheduled arrival, submission, launch, done (server clock)
+    t_submit_ns: int = 0
+    t_launch_ns: int = 0
+    t_done_ns: int = 0
 
 
 class Lane:
@@ -208,6 +214,85 @@ class Server:
             l.tracker.close()
 
 
+class NativeServer:
+    """The native serving loop (``tpc_server_*``): lanes, batch forming, copies and the per-event
+    split run in the library's own thread; Python only submits events and collects results."""
+
+    def __init__(self, geometry, lanes=3, hbm_budget=40 << 30, max_batch=16, lane_clusters=None, params=None):
+        if lane_clusters is None:
+            lane_clusters = int(hbm_budget / lanes / BYTES_PER_CLUSTER)
+        self.lane_clusters = lane_clusters
+        self.max_batch = max_batch
+        self.handle = tpc_server_create(geometry.row_x, geometry.tan_half, geometry.z_max, geometry.n_sectors,
+                                        geometry.bz, lanes, max_batch, lane_clusters, hbm_budget, params)
+        self.inflight = {}
+        self.done = []
+        self.rejected = []
+        self.high_water = 0
+
+    def submit(self, r: Request, arrival_ns=None):
+        try:
+            rid = tpc_server_submit(self.handle, r.y, r.z, r.row, r.counts, r.n)
+        except TrackerError:
+            r.status = "rejected"
+            self.rejected.append(r)
+            return False
+        r.arrival_ns = arrival_ns
+        self.inflight[rid] = r
+        self.high_water = max(self.high_water, len(self.inflight))
+        return True
+
+    def poll(self, now=None):
+        ids = tpc_server_poll(self.handle)
+        for rid in ids:
+            r = self.inflight.pop(rid)
+            res = tpc_server_get(self.handle, rid)
+            r.status = "done" if res.status == 0 else "error %d" % res.status
+            r.result = server_result_arrays(res) if res.status == 0 else None
+            r.batch_size = res.batch_size
+            r.t_submit_ns, r.t_launch_ns, r.t_done_ns = res.t_submit_ns, res.t_launch_ns, res.t_done_ns
+            tpc_server_release(self.handle, rid)
+            self.done.append(r)
+        return bool(ids)
+
+    def busy(self):
+        return bool(self.inflight)
+
+    def warm(self, requests):
+        """A burst of events through every lane before measuring (first-use costs of each lane)."""
+        batch = [r for r in requests[:self.max_batch * 4]]
+        for r in batch:
+            self.submit(dataclasses.replace(r))
+        while self.busy():
+            self.poll()
+            time.sleep(50e-6)
+        self.done.clear()
+
+    def close(self):
+        tpc_server_destroy(self.handle)
+
+
+def run_stream_native(server: NativeServer, requests, realtime=True, idle_sleep=20e-6):
+    """Submit requests at their arrival times (the server's clock) and collect them as they finish.
+    Latency t_done - t_arrival counts any delay of the submission too."""
+    reqs = sorted(requests, key=lambda r: r.arrival)
+    t0 = tpc_server_now_ns()
+    i = 0
+    while i < len(reqs) or server.busy():
+        now = (tpc_server_now_ns() - t0) * 1e-9
+        while i < len(reqs) and (reqs[i].arrival <= now or not realtime):
+            server.submit(reqs[i], arrival_ns=t0 + int(reqs[i].arrival * 1e9) if realtime else tpc_server_now_ns())
+            i += 1
+        if not server.poll():
+            nxt = reqs[i].arrival - now if i < len(reqs) and realtime else idle_sleep
+            time.sleep(min(idle_sleep, max(0.0, nxt)))
+    for r in reqs:
+        if r.status == "done":
+            r.t_done = (r.t_done_ns - t0) * 1e-9
+            r.arrival = (r.arrival_ns - t0) * 1e-9
+    return (tpc_server_now_ns() - t0) * 1e-9
+
+
 def run_stream(server: Server, requests, realtime=True, idle_sleep=20e-6):
     """Feed requests at their arrival times (wall clock) and run until all are finished."""
     t0 = time.perf_counter()
@@ -288,19 +373,21 @@ def main():
     ap.add_argument("--lanes", type=int, default=3)
     ap.add_argument("--max-batch", type=int, default=16)
     ap.add_argument("--budget-gb", type=float, default=40.0)
+    ap.add_argument("--python", action="store_true", help="the Python loop instead of the native server")
     a = ap.parse_args()
     pool = event_pool(a.pool)
     geo = eventgen.Geometry()
     for rate in [float(r) for r in a.rates.split(",")]:
         for mode in ("batched", "per-event"):
             lanes, mb = (a.lanes, a.max_batch) if mode == "batched" else (1, 1)
-            srv = Server(geo, lanes=lanes, hbm_budget=int(a.budget_gb * (1 << 30)), max_batch=mb)
+            cls = Server if a.python else NativeServer
+            srv = cls(geo, lanes=lanes, hbm_budget=int(a.budget_gb * (1 << 30)), max_batch=mb)
             srv.warm(make_requests(pool, np.zeros(len(pool)), seed=99))
             reqs = make_requests(pool, poisson_arrivals(rate, a.duration, seed=int(rate)), seed=int(rate))
-            wall = run_stream(srv, reqs)
+            wall = (run_stream if a.python else run_stream_native)(srv, reqs)
             rep = latency_report(reqs, wall)
             rep.update(rate_hz=rate, mode=mode, lanes=lanes, max_batch=mb, budget_gb=a.budget_gb,
-                       queue_high_water=srv.high_water)
+                       queue_high_water=srv.high_water, loop="python" if a.python else "native")
             print(json.dumps(rep), flush=True)
             srv.close()
             torch.cuda.synchronize()

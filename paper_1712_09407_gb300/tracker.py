@@ -68,6 +68,16 @@ class tpc_call_stats(ctypes.Structure):
                 ("global_found", c_int64), ("graph_builds", c_int64), ("sector_tracks", c_int64)]
 
 
+class tpc_server_config(ctypes.Structure):
+    _fields_ = [("lanes", c_int), ("max_batch", c_int), ("lane_clusters", c_int64), ("hbm_budget", ctypes.c_size_t)]
+
+
+class tpc_server_result(ctypes.Structure):
+    _fields_ = [("status", c_int), ("n_tracks", c_int64), ("n_hits", c_int64)] + [
+        (n, c_void_p) for n in ("par", "cov", "x_ref", "alpha", "chi2", "ndf", "nhits", "first", "sector", "hits")] + [
+        ("t_submit_ns", c_int64), ("t_launch_ns", c_int64), ("t_done_ns", c_int64), ("batch_size", c_int)]
+
+
 EXPORTS = {
     "tpc_params_default": (None, [P(tpc_params)]),
     "tpc_tuning_default": (None, [P(tpc_tuning)]),
@@ -93,6 +103,13 @@ EXPORTS = {
     "tpc_result_stats": (c_int, [c_void_p, P(tpc_call_stats)]),
     "tpc_find_links_noalloc": (c_int, [c_void_p, c_void_p, c_void_p, c_void_p, c_void_p, c_int64, c_void_p,
                                        c_void_p, c_void_p, c_void_p]),
+    "tpc_server_create": (c_int, [P(tpc_geometry), c_float, P(tpc_params), P(tpc_server_config), P(c_void_p)]),
+    "tpc_server_submit": (c_int, [c_void_p, c_void_p, c_void_p, c_void_p, c_void_p, c_int64, P(c_int64)]),
+    "tpc_server_poll": (c_int, [c_void_p, P(c_int64), c_int, P(c_int)]),
+    "tpc_server_get": (c_int, [c_void_p, c_int64, P(tpc_server_result)]),
+    "tpc_server_release": (c_int, [c_void_p, c_int64]),
+    "tpc_server_now_ns": (c_int64, []),
+    "tpc_server_destroy": (None, [c_void_p]),
 }
 
 
@@ -227,6 +244,69 @@ def tpc_result_copy_to_host(res, arrays: dict):
 
 def tpc_result_release(res):
     lib().tpc_result_release(res)
+
+
+def tpc_server_create(row_x, tan_half, z_max, n_sectors, bz, lanes, max_batch, lane_clusters, hbm_budget=0,
+                      params=None):
+    rx = np.ascontiguousarray(row_x, dtype=np.float32)
+    g = tpc_geometry(int(rx.shape[0]), rx.ctypes.data_as(P(c_float)), float(tan_half), float(z_max), int(n_sectors))
+    cfg = tpc_server_config(int(lanes), int(max_batch), int(lane_clusters), int(hbm_budget))
+    h = c_void_p()
+    _check(lib().tpc_server_create(ctypes.byref(g), float(bz), ctypes.byref(params) if params is not None else None,
+                                   ctypes.byref(cfg), ctypes.byref(h)), "tpc_server_create")
+    return h
+
+
+def tpc_server_submit(srv, y, z, row, counts, n) -> int:
+    """Queue one event (host arrays that must stay alive until it is done); returns its id."""
+    counts = np.ascontiguousarray(counts, dtype=np.int32)
+    i = c_int64()
+    _check(lib().tpc_server_submit(srv, _ptr(y), _ptr(z), _ptr(row), counts.ctypes.data, int(n), ctypes.byref(i)),
+           "tpc_server_submit")
+    return int(i.value)
+
+
+def tpc_server_poll(srv, max_ids=1024):
+    ids = (c_int64 * max_ids)()
+    n = c_int()
+    _check(lib().tpc_server_poll(srv, ids, int(max_ids), ctypes.byref(n)), "tpc_server_poll")
+    return [int(ids[i]) for i in range(n.value)]
+
+
+def tpc_server_get(srv, rid) -> tpc_server_result:
+    r = tpc_server_result()
+    _check(lib().tpc_server_get(srv, int(rid), ctypes.byref(r)), "tpc_server_get")
+    return r
+
+
+def tpc_server_release(srv, rid):
+    _check(lib().tpc_server_release(srv, int(rid)), "tpc_server_release")
+
+
+def tpc_server_now_ns() -> int:
+    return int(lib().tpc_server_now_ns())
+
+
+def tpc_server_destroy(srv):
+    lib().tpc_server_destroy(srv)
+
+
+def server_result_arrays(r: tpc_server_result) -> dict:
+    """Copies of a finished event's host arrays."""
+    M, H = r.n_tracks, r.n_hits
+
+    def arr(ptr, count, ctype, dtype, shape=None):
+        if count == 0 or not ptr:
+            a = np.zeros(count, dtype=dtype)
+        else:
+            a = np.frombuffer((ctype * count).from_address(ptr), dtype=dtype, count=count).copy()
+        return a.reshape(shape) if shape else a
+
+    f, i = ctypes.c_float, ctypes.c_int32
+    return dict(par=arr(r.par, M * 5, f, np.float32, (M, 5)), cov=arr(r.cov, M * 15, f, np.float32, (M, 15)),
+                x_ref=arr(r.x_ref, M, f, np.float32), alpha=arr(r.alpha, M, f, np.float32),
+                chi2=arr(r.chi2, M, f, np.float32), ndf=arr(r.ndf, M, i, np.int32), nhits=arr(r.nhits, M, i, np.int32),
+                first=arr(r.first, M, i, np.int32), sector=arr(r.sector, M, i, np.int32), hits=arr(r.hits, H, i, np.int32))
 
 
 def tpc_tracker_destroy(tr):
