@@ -217,7 +217,7 @@ int launch_global(const DevConst &c, const Workspace &w, int64_t n_slots, const 
     cudaMemsetAsync(w.gkey, 0, (size_t)n_slots * sizeof(unsigned long long), s);
     const int grid = lc.num_sms * 8;
     k_global_used<<<grid, 256, 0, s>>>(c, w);
-    k_global_find<<<lc.num_sms * 16, kGlobalBlock, 0, s>>>(c, w);
+    k_global_find<<<lc.num_sms * 32, kGlobalBlock, 0, s>>>(c, w);    // one round for 2 x 300 k tracklets
     const int scans = launch_scan_i32(w.g_n, w.g_off, 2 * w.tcap, w.counters + CNT_GLIST, w.scan_tmp, nullptr, s);
     k_global_place<<<grid, 256, 0, s>>>(w);
     return 3 + scans;

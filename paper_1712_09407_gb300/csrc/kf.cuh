@@ -235,8 +235,8 @@ __device__ __forceinline__ int search_cells(const DevConst &c, const float2 *yz,
         const int a = cell[iz * ny + iy0], e = cell[iz * ny + iy1 + 1];
         ncand += e - a;
         for (int j = a; j < e; j++) {
+            const float2 q = yz[j];                     // issued together with the used[] load
             if (used && used[j]) continue;
-            const float2 q = yz[j];
             if (!(fabsf(q.x - y) <= wy && fabsf(q.y - z) <= wz)) continue;
             const float x2 = chi2_of(g, q.x - y, q.y - z);
             if (best < 0 || x2 < bc) {
