@@ -235,16 +235,46 @@ __global__ void __launch_bounds__(kMergeBlock) k_mg_scatter(const Workspace w)
         if (w.rf_ok[m]) w.mg_by_sec[atomicAdd(&w.mg_sec_cur[w.rf_sin[m]], 1)] = m;
 }
 
+// chi2 of outer end `ar` (track a, already in b's frame at x = xa) with track b's inner end;
+// false if the transport fails, the sum is not positive definite or the gate is not passed.
+__device__ __forceinline__ bool match_pair(const DevConst &c, const Workspace &w, const KF &ar, float xa, int b,
+                                           float &chi2)
+{
+    const int64_t T = w.tcap;
+    const float xb = w.rf_xin[b];
+    KF pr = ar;
+    if (xa != xb && !propagate(pr, xb - xa, c)) return false;
+    KF bs;
+    kf_load(w.rf_P, w.rf_C, T, b, bs);
+    float A[15], Bc[15], d[5];
+    kf_to15(pr, A);
+    kf_to15(bs, Bc);
+#pragma unroll
+    for (int i = 0; i < 15; i++) A[i] = A[i] + Bc[i];
+    d[0] = bs.p0 - pr.p0;
+    d[1] = bs.p1 - pr.p1;
+    d[2] = bs.p2 - pr.p2;
+    d[3] = bs.p3 - pr.p3;
+    d[4] = bs.p4 - pr.p4;
+    return chi2_5(A, d, chi2) && chi2 <= c.mchi2;
+}
+
 // Best partner of every outer end; best partner of every inner end by atomicMin.  One warp per
 // outer end: the lanes sweep the candidate sectors' lists 32 tracks at a time (coalesced index
-// loads, the radial-gap gate first), the passing lanes run the transport and the chi2, and the
-// warp's best is the minimum of (chi2 bits, track) over its lanes; chi2 >= 0, so the bits order
-// like the values and equal chi2 go to the lower track, as in a sequential scan.
+// loads) through the cheap gates (radial gap, q/pT); the survivors go to a per-warp queue in
+// shared memory, and whenever it holds 32 of them the whole warp runs the transport and the
+// chi2, so the expensive part executes with all lanes busy.  The warp's best is the minimum of
+// (chi2 bits, track) over its lanes; chi2 >= 0, so the bits order like the values and equal chi2
+// go to the lower track, whatever order the candidates were evaluated in.
+constexpr int kMatchWarps = kMergeBlock / 32;
+
 __global__ void __launch_bounds__(kMergeBlock) k_mg_match(const DevConst c, const Workspace w)
 {
+    __shared__ int queue[kMatchWarps][64];
     const int M = w.counters[CNT_TRACKS];
     const int64_t T = w.tcap;
     const int lane = threadIdx.x & 31;
+    int *qu = queue[threadIdx.x >> 5];
     const int nwarps = (gridDim.x * blockDim.x) >> 5;
     for (int a = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; a < M; a += nwarps) {
         unsigned long long best = ~0ull;
@@ -252,6 +282,7 @@ __global__ void __launch_bounds__(kMergeBlock) k_mg_match(const DevConst c, cons
             const int sa = w.rf_sout[a];
             const int ev = sa / 36, side = (sa % 36) / 18, az = sa % 18;
             const float r_out = w.rf_rout[a];
+            const float aq = w.rf_oP[4 * T + a], ac44 = w.rf_oC[14 * T + a];   // unchanged by the rotation
             for (int q = 0; q < 3; q++) {
                 const int sb = ev * 36 + (q == 0 ? (1 - side) * 18 + az
                                                  : side * 18 + (q == 1 ? (az + 1) % 18 : (az + 17) % 18));
@@ -262,36 +293,45 @@ __global__ void __launch_bounds__(kMergeBlock) k_mg_match(const DevConst c, cons
                 float xa = w.rf_xout[a];
                 int sc = sa;
                 if (!to_frame(c, ar, xa, sc, sb)) continue;       // the same for every lane
+                int count = 0;                                      // warp-uniform queue length
                 for (int i0 = b0; i0 < b1; i0 += 32) {
                     const int ib = i0 + lane;
                     const int b = ib < b1 ? w.mg_by_sec[ib] : a;
-                    if (b == a) continue;
-                    const float gap = w.rf_rin[b] - r_out;
-                    if (!(gap > 0.0f && gap <= c.mgap)) continue;
-                    const float bq = w.rf_P[4 * T + b], bc44 = w.rf_C[14 * T + b];
-                    const float dq = bq - ar.p4;
-                    if (!(dq * dq <= c.mq2 * (ar.c44 + bc44))) continue;
-                    const float xb = w.rf_xin[b];
-                    KF pr = ar;
-                    if (xa != xb && !propagate(pr, xb - xa, c)) continue;
-                    KF bs;
-                    kf_load(w.rf_P, w.rf_C, T, b, bs);
-                    float A[15], Bc[15], d[5];
-                    kf_to15(pr, A);
-                    kf_to15(bs, Bc);
-#pragma unroll
-                    for (int i = 0; i < 15; i++) A[i] = A[i] + Bc[i];
-                    d[0] = bs.p0 - pr.p0;
-                    d[1] = bs.p1 - pr.p1;
-                    d[2] = bs.p2 - pr.p2;
-                    d[3] = bs.p3 - pr.p3;
-                    d[4] = bs.p4 - pr.p4;
-                    float chi2;
-                    if (!chi2_5(A, d, chi2) || !(chi2 <= c.mchi2)) continue;
-                    const unsigned long long key = ((unsigned long long)__float_as_uint(chi2) << 32) | (unsigned)b;
-                    if (key < best) best = key;
-                    atomicMin(&w.mg_bkey[b], ((unsigned long long)__float_as_uint(chi2) << 32) | (unsigned)a);
+                    bool pass = b != a;
+                    if (pass) {
+                        const float gap = w.rf_rin[b] - r_out;
+                        pass = gap > 0.0f && gap <= c.mgap;
+                    }
+                    if (pass) {
+                        const float dq = w.rf_P[4 * T + b] - aq;
+                        pass = dq * dq <= c.mq2 * (ac44 + w.rf_C[14 * T + b]);
+                    }
+                    const unsigned mask = __ballot_sync(kFull, pass);
+                    if (pass) qu[count + __popc(mask & lanemask_lt())] = b;
+                    count += __popc(mask);
+                    __syncwarp();
+                    if (count >= 32) {
+                        const int bb = qu[count - 32 + lane];
+                        float chi2;
+                        if (match_pair(c, w, ar, xa, bb, chi2)) {
+                            const unsigned long long key = ((unsigned long long)__float_as_uint(chi2) << 32) | (unsigned)bb;
+                            if (key < best) best = key;
+                            atomicMin(&w.mg_bkey[bb], ((unsigned long long)__float_as_uint(chi2) << 32) | (unsigned)a);
+                        }
+                        count -= 32;
+                        __syncwarp();
+                    }
                 }
+                if (lane < count) {
+                    const int bb = qu[lane];
+                    float chi2;
+                    if (match_pair(c, w, ar, xa, bb, chi2)) {
+                        const unsigned long long key = ((unsigned long long)__float_as_uint(chi2) << 32) | (unsigned)bb;
+                        if (key < best) best = key;
+                        atomicMin(&w.mg_bkey[bb], ((unsigned long long)__float_as_uint(chi2) << 32) | (unsigned)a);
+                    }
+                }
+                __syncwarp();
             }
         }
 #pragma unroll

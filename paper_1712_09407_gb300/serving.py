@@ -218,9 +218,11 @@ class NativeServer:
     """The native serving loop (``tpc_server_*``): lanes, batch forming, copies and the per-event
     split run in the library's own thread; Python only submits events and collects results."""
 
-    def __init__(self, geometry, lanes=3, hbm_budget=40 << 30, max_batch=16, lane_clusters=None, params=None):
+    def __init__(self, geometry, lanes=3, hbm_budget=40 << 30, max_batch=16, lane_clusters=None, params=None,
+                 keep_results=True):
         if lane_clusters is None:
             lane_clusters = int(hbm_budget / lanes / BYTES_PER_CLUSTER)
+        self.keep_results = keep_results           # False: record status and timing only (load tests)
         self.lane_clusters = lane_clusters
         self.max_batch = max_batch
         self.handle = tpc_server_create(geometry.row_x, geometry.tan_half, geometry.z_max, geometry.n_sectors,
@@ -248,7 +250,7 @@ class NativeServer:
             r = self.inflight.pop(rid)
             res = tpc_server_get(self.handle, rid)
             r.status = "done" if res.status == 0 else "error %d" % res.status
-            r.result = server_result_arrays(res) if res.status == 0 else None
+            r.result = server_result_arrays(res) if res.status == 0 and self.keep_results else None
             r.batch_size = res.batch_size
             r.t_submit_ns, r.t_launch_ns, r.t_done_ns = res.t_submit_ns, res.t_launch_ns, res.t_done_ns
             tpc_server_release(self.handle, rid)
@@ -275,7 +277,10 @@ class NativeServer:
 def run_stream_native(server: NativeServer, requests, realtime=True, idle_sleep=20e-6):
     """Submit requests at their arrival times (the server's clock) and collect them as they finish.
     Latency t_done - t_arrival counts any delay of the submission too."""
+    import gc
     reqs = sorted(requests, key=lambda r: r.arrival)
+    gc_was = gc.isenabled()
+    gc.disable()                                   # no collector pauses between submissions
     t0 = tpc_server_now_ns()
     i = 0
     while i < len(reqs) or server.busy():
@@ -286,11 +291,14 @@ def run_stream_native(server: NativeServer, requests, realtime=True, idle_sleep=
         if not server.poll():
             nxt = reqs[i].arrival - now if i < len(reqs) and realtime else idle_sleep
             time.sleep(min(idle_sleep, max(0.0, nxt)))
+    wall = (tpc_server_now_ns() - t0) * 1e-9
+    if gc_was:
+        gc.enable()
     for r in reqs:
         if r.status == "done":
             r.t_done = (r.t_done_ns - t0) * 1e-9
             r.arrival = (r.arrival_ns - t0) * 1e-9
-    return (tpc_server_now_ns() - t0) * 1e-9
+    return wall
 
 
 def run_stream(server: Server, requests, realtime=True, idle_sleep=20e-6):
@@ -380,8 +388,11 @@ def main():
     for rate in [float(r) for r in a.rates.split(",")]:
         for mode in ("batched", "per-event"):
             lanes, mb = (a.lanes, a.max_batch) if mode == "batched" else (1, 1)
-            cls = Server if a.python else NativeServer
-            srv = cls(geo, lanes=lanes, hbm_budget=int(a.budget_gb * (1 << 30)), max_batch=mb)
+            if a.python:
+                srv = Server(geo, lanes=lanes, hbm_budget=int(a.budget_gb * (1 << 30)), max_batch=mb)
+            else:
+                srv = NativeServer(geo, lanes=lanes, hbm_budget=int(a.budget_gb * (1 << 30)), max_batch=mb,
+                                   keep_results=False)
             srv.warm(make_requests(pool, np.zeros(len(pool)), seed=99))
             reqs = make_requests(pool, poisson_arrivals(rate, a.duration, seed=int(rate)), seed=int(rate))
             wall = (run_stream if a.python else run_stream_native)(srv, reqs)
