@@ -47,7 +47,8 @@ enum {
     TPC_ERR_BUDGET = 3,        /* the call would exceed the tracker's HBM budget */
     TPC_ERR_TIMEOUT = 4,       /* a bounded device-side wait expired */
     TPC_ERR_CUDA = 5,          /* a CUDA runtime call failed */
-    TPC_ERR_STATE = 6          /* wrong call order (e.g. reading a result before it was produced) */
+    TPC_ERR_STATE = 6,         /* wrong call order (e.g. reading a result before it was produced) */
+    TPC_ERR_CHECK = 7          /* an index bounds check of the checked build failed (internal error) */
 };
 
 /* Pipeline stages, as reported by tpc_last_error_detail. */

@@ -8,10 +8,20 @@
 #include <new>
 #include <vector>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "common.cuh"
 #include "../../include/tpcca.h"
 
 using namespace tpc;
+
+namespace {
+// NVTX range for the host side of a call (visible in nsys/ncu timelines; free when no tool listens).
+struct NvtxRange {
+    explicit NvtxRange(const char *name) { nvtxRangePushA(name); }
+    ~NvtxRange() { nvtxRangePop(); }
+};
+}  // namespace
 
 namespace {
 
@@ -183,6 +193,7 @@ extern "C" const char *tpc_status_string(int s)
     case TPC_ERR_TIMEOUT: return "bounded device wait expired";
     case TPC_ERR_CUDA: return "CUDA runtime error";
     case TPC_ERR_STATE: return "invalid call order";
+    case TPC_ERR_CHECK: return "index bounds check failed (checked build)";
     default: return "unknown status";
     }
 }
@@ -372,6 +383,8 @@ static size_t carve(tpc_tracker *tr, const WsSizes &s, Alloc &a)
         w.st.sector = a.take<int32_t>(s.T);
         w.st.event = a.take<int32_t>(s.T);
         w.st.hits = a.take<int32_t>(s.P);
+        w.st.mcap = s.T;
+        w.st.hcap = s.P;
         w.rf_ok = a.take<int32_t>(s.T);
         w.rf_sin = a.take<int32_t>(s.T);
         w.rf_sout = a.take<int32_t>(s.T);
@@ -481,6 +494,8 @@ static void carve_result(tpc_result *r, int64_t tcap, int64_t ncap)
     r->out.sector = a.take<int32_t>(tcap);
     r->out.event = a.take<int32_t>(tcap);
     r->out.hits = a.take<int32_t>(ncap > 0 ? ncap : 1);
+    r->out.mcap = tcap;
+    r->out.hcap = ncap;
 }
 
 static int run(tpc_tracker *tr, const float *y, const float *z, const uint8_t *row, const int32_t *counts,
@@ -655,6 +670,7 @@ static int run(tpc_tracker *tr, const float *y, const float *z, const uint8_t *r
     chk(cudaMemsetAsync(w.ckey, 0, s_off * sizeof(unsigned long long), ls));
 
     int launches = 0;
+    NvtxRange nvtx_call(graph ? "tpc: capture call" : "tpc: launch call");
     mark(1);
     launches += launch_ingest(tr->dc, w, y, z, row, R, ls);
     mark(2);
@@ -713,6 +729,7 @@ extern "C" int tpc_track_batch(tpc_tracker *tr, const float *y, const float *z, 
                                const int32_t *counts, int n_events, int64_t n_total, void *stream,
                                tpc_result **out)
 {
+    NvtxRange nvtx("tpc_track_batch");
     if (!tr || !out || !counts || n_events < 1 || n_total < 0) return TPC_ERR_INVALID_ARG;
     *out = nullptr;
     std::lock_guard<std::mutex> g(tr->mu);

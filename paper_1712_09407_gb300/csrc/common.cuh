@@ -67,6 +67,7 @@ struct DevConst {
 struct OutBuffers {
     float *par, *cov, *x, *alpha, *chi2;
     int32_t *ndf, *nhits, *first, *sector, *event, *hits;
+    int64_t mcap, hcap;    // tracks and hits the buffers hold
 };
 
 // Per row unit metadata (host-computed): input offset, count, sorted offset, cell offset.
@@ -159,6 +160,21 @@ __device__ __forceinline__ void set_error(int32_t *err, int status, int unit, co
         err[ERR_STAGE] = stage;
     }
 }
+
+// Index checks of the checked build (-DTPC_CHECKED, the library built next to the release one):
+// an index outside its pool records TPC_ERR_CHECK with the stage and the access is skipped.  The
+// release build compiles them to `true`.
+#ifdef TPC_CHECKED
+__device__ __forceinline__ bool idx_ok(int64_t i, int64_t n, int32_t *err, int stage)
+{
+    if (i >= 0 && i < n) return true;
+    if (atomicCAS(&err[ERR_STATUS], 0, 7) == 0) err[ERR_STAGE] = stage;
+    return false;
+}
+#define TPC_IDX(i, n, err, c, stage) ::tpc::idx_ok((int64_t)(i), (int64_t)(n), (err), (stage))
+#else
+#define TPC_IDX(i, n, err, c, stage) true
+#endif
 
 // Monotone map of a float to an unsigned integer (larger float -> larger integer).
 __device__ __forceinline__ uint32_t ordered_bits(float f)

@@ -66,7 +66,7 @@ __global__ void __launch_bounds__(256) k_order_scatter(const DevConst c, const W
     const int T = n_tracklets(w);
     for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < T; t += gridDim.x * blockDim.x) {
         const int pos = atomicAdd(&w.buckets[kOrderBuckets + work_key(c, w.starts[t].w)], 1);
-        w.order[pos] = t;
+        if (TPC_IDX(pos, T, w.err, c, 4)) w.order[pos] = t;
     }
 }
 
@@ -125,7 +125,7 @@ k_construct(const DevConst c, const Workspace w)
                 const float2 q = __ldg(w.yz + b);
                 if (phase == 2) {
                     chi2sum = chi2sum + chi2;
-                    w.tl_hits[(int64_t)t * c.nr + n] = b;
+                    if (TPC_IDX(n, c.nr, w.err, c, 4)) w.tl_hits[(int64_t)t * c.nr + n] = b;
                     n++;
                 } else {
                     rlast = r;

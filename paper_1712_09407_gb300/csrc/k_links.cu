@@ -95,7 +95,7 @@ k_ingest(const DevConst c, const Workspace w, const float *__restrict__ yin, con
             __syncwarp();
             if (v && rank == 0) hist[cc] = base + __popc(peers);
             __syncwarp();
-            if (v) {
+            if (v && TPC_IDX(s_off + base + rank, w.pcap, w.err, c, 1)) {
                 w.yz[s_off + base + rank] = make_float2(y, z);
                 w.orig[s_off + base + rank] = in_off + i;
             }

@@ -201,7 +201,8 @@ __global__ void __launch_bounds__(256) k_mg_prep(const DevConst c, const Workspa
     for (int64_t u = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; u < R; u += nwarps) {
         const int4 m = w.meta[u];
         const int s = (int)(u / c.nr);
-        for (int i = lane; i < m.y; i += 32) w.in_sec[m.x + i] = s;
+        for (int i = lane; i < m.y; i += 32)
+            if (TPC_IDX(m.x + i, w.pcap, w.err, c, 8)) w.in_sec[m.x + i] = s;
     }
 }
 
@@ -232,7 +233,10 @@ __global__ void __launch_bounds__(kMergeBlock) k_mg_scatter(const Workspace w)
 {
     const int M = w.counters[CNT_TRACKS];
     for (int m = blockIdx.x * blockDim.x + threadIdx.x; m < M; m += gridDim.x * blockDim.x)
-        if (w.rf_ok[m]) w.mg_by_sec[atomicAdd(&w.mg_sec_cur[w.rf_sin[m]], 1)] = m;
+        if (w.rf_ok[m]) {
+            const int at = atomicAdd(&w.mg_sec_cur[w.rf_sin[m]], 1);
+            if (TPC_IDX(at, w.tcap, w.err, c, 8)) w.mg_by_sec[at] = m;
+        }
 }
 
 // chi2 of outer end `ar` (track a, already in b's frame at x = xa) with track b's inner end;
@@ -380,10 +384,12 @@ __global__ void __launch_bounds__(256) k_mg_write(const Workspace w, const OutBu
         if (w.mg_prev[m] >= 0) continue;
         const int j = w.mg_idx[m];
         const int f = w.mg_first[m];
+        if (!TPC_IDX(j, o.mcap, w.err, c, 8)) continue;
         int pos = f, nseg = 0, t = m;
         for (int k = 0; k < kMaxChain && t >= 0; k++, t = w.mg_next[t]) {
             const int n = w.st.nhits[t], s0 = w.st.first[t];
-            for (int i = lane; i < n; i += 32) o.hits[pos + i] = w.st.hits[s0 + i];
+            for (int i = lane; i < n; i += 32)
+                if (TPC_IDX(pos + i, o.hcap, w.err, c, 8)) o.hits[pos + i] = w.st.hits[s0 + i];
             pos += n;
             nseg++;
         }

@@ -231,7 +231,8 @@ __device__ __forceinline__ int write_prolongation(const Workspace &w, const OutB
         const int i = reverse ? n - 1 - (i0 + lane) : i0 + lane;
         const bool own = i >= 0 && i < n && w.gkey[h[i]] == key;
         const unsigned mask = __ballot_sync(kFull, own);
-        if (own) o.hits[pos + __popc(mask & lanemask_lt())] = w.orig[h[i]];
+        if (own && TPC_IDX(pos + __popc(mask & lanemask_lt()), o.hcap, w.err, c, 6))
+            o.hits[pos + __popc(mask & lanemask_lt())] = w.orig[h[i]];
         pos += __popc(mask);
     }
     return pos;
@@ -244,6 +245,7 @@ __global__ void __launch_bounds__(256) k_write(const DevConst c, const Workspace
     const int nwarps = (gridDim.x * blockDim.x) >> 5;
     const int tcap = (int)w.tcap;
     for (int m = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; m < M; m += nwarps) {
+        if (!TPC_IDX(m, o.mcap, w.err, c, 6)) continue;
         const int t = w.rank_trk[m];
         const int first = w.rank_first[m];
         const unsigned long long key = w.tl_key[t];
@@ -285,7 +287,8 @@ __global__ void __launch_bounds__(256) k_write(const DevConst c, const Workspace
             const int i = n - 1 - (i0 + lane);
             const bool own = i >= 0 && w.ckey[h[i]] == key;
             const unsigned mask = __ballot_sync(kFull, own);
-            if (own) o.hits[pos + __popc(mask & lanemask_lt())] = w.orig[h[i]];
+            if (own && TPC_IDX(pos + __popc(mask & lanemask_lt()), o.hcap, w.err, c, 6))
+            o.hits[pos + __popc(mask & lanemask_lt())] = w.orig[h[i]];
             pos += __popc(mask);
         }
         // outward prolongation's clusters, in search order (inner to outer)

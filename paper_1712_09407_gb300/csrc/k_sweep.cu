@@ -185,7 +185,7 @@ __global__ void __launch_bounds__(256) k_sw_scatter(const Workspace w, int n_sec
     const int T = n_tracklets(w);
     for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < T; t += gridDim.x * blockDim.x) {
         const int pos = atomicAdd(&w.sw_sec[n_sec + (w.starts[t].w >> 16)], 1);
-        w.order[pos] = t;
+        if (TPC_IDX(pos, T, w.err, c, 4)) w.order[pos] = t;
     }
 }
 
@@ -347,7 +347,8 @@ __global__ void __launch_bounds__(kSwThreads, 2) k_construct_sweep(const DevCons
                         if (bl >= 0 && chi2 <= c.chi2max) {
                             if (!up) {
                                 S.chi[i] = S.chi[i] + chi2;
-                                w.tl_hits[(int64_t)S.t[i] * c.nr + S.n[i]] = rg.x + bl;
+                                if (TPC_IDX(S.n[i], c.nr, w.err, c, 4))
+                                    w.tl_hits[(int64_t)S.t[i] * c.nr + S.n[i]] = rg.x + bl;
                                 S.n[i] = S.n[i] + 1;
                             } else {
                                 S.rlast[i] = r;

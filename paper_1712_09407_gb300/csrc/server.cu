@@ -22,6 +22,7 @@
 #include <vector>
 
 #include <cuda_runtime.h>
+#include <nvtx3/nvToolsExt.h>
 #include "../../include/tpcca.h"
 
 namespace {
@@ -163,6 +164,7 @@ void split(Lane &L)
 
 bool launch(tpc_server *s, Lane &L, std::vector<Req *> &batch)
 {
+    nvtxRangePushA("tpc_server: launch batch");
     L.batch = batch;
     L.offs.clear();
     L.counts.clear();
@@ -180,6 +182,7 @@ bool launch(tpc_server *s, Lane &L, std::vector<Req *> &batch)
         r->t_launch = t;
     }
     const int st = tpc_track_batch(L.tr, L.dy, L.dz, L.drow, L.counts.data(), (int)batch.size(), off, L.st, &L.res);
+    nvtxRangePop();
     if (st != TPC_OK) {
         for (Req *r : batch) {
             r->status = st;
@@ -234,7 +237,9 @@ void loop(tpc_server *s)
                 }
                 moved = true;
             } else if (L.state == 2 && cudaEventQuery(L.copied) == cudaSuccess) {
+                nvtxRangePushA("tpc_server: split result");
                 split(L);
+                nvtxRangePop();
                 tpc_result_release(L.res);
                 L.res = nullptr;
                 for (Req *r : L.batch) finish(s, r);

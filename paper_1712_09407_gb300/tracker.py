@@ -20,7 +20,8 @@ from . import build as _build
 _lock = threading.Lock()
 _lib = None
 
-TPC_OK, TPC_ERR_INVALID_ARG, TPC_ERR_CAPACITY, TPC_ERR_BUDGET, TPC_ERR_TIMEOUT, TPC_ERR_CUDA, TPC_ERR_STATE = range(7)
+(TPC_OK, TPC_ERR_INVALID_ARG, TPC_ERR_CAPACITY, TPC_ERR_BUDGET, TPC_ERR_TIMEOUT, TPC_ERR_CUDA, TPC_ERR_STATE,
+ TPC_ERR_CHECK) = range(8)
 STAGES = {0: "none", 1: "ingest", 2: "neighbours", 3: "evolution", 4: "construction", 5: "selection", 6: "output",
           7: "global", 8: "merge"}
 
@@ -127,14 +128,16 @@ def _status_text(s):
 
 
 def lib():
-    """Load libtpcca.so (built in-tree).  Raises if it has not been built."""
+    """Load libtpcca.so (built in-tree; TPCCA_LIB may name the checked build instead).  Raises if it
+    has not been built."""
     global _lib
     with _lock:
         if _lib is None:
-            if not os.path.exists(_build.LIB):
-                raise RuntimeError("libtpcca.so is not built: run __graft_entry__.build() "
-                                   "(the tracker has no CPU fallback)")
-            L = ctypes.CDLL(_build.LIB)
+            path = os.environ.get("TPCCA_LIB", _build.LIB)
+            if not os.path.exists(path):
+                raise RuntimeError("%s is not built: run __graft_entry__.build() "
+                                   "(the tracker has no CPU fallback)" % os.path.basename(path))
+            L = ctypes.CDLL(path)
             for name, (res, args) in EXPORTS.items():
                 f = getattr(L, name)
                 f.restype = res

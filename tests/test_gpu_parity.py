@@ -391,3 +391,14 @@ def test_result_outlives_its_tracker():
     tr.close()                                   # destroys the tracker while the result is held
     assert len(out["first"]) == m > 0
     res.release()
+
+
+def test_clusters_per_track_distribution(both1):
+    """Section 3.3 / Fig. "gp_sizesum": the clusters-per-track statistic of the GPU and the CPU
+    tracker agree (here bin for bin, the outputs being identical)."""
+    ev, out, dbg, ref = both1
+    bins = np.arange(30, 161)
+    hg, _ = np.histogram(out["nhits"], bins=bins)
+    ho, _ = np.histogram(ref.trk_nhits, bins=bins)
+    assert hg.sum() == ho.sum() > 1000
+    assert np.array_equal(hg, ho)
