@@ -61,12 +61,30 @@ __global__ void __launch_bounds__(kOrderBuckets) k_order_scan(const Workspace w)
     w.buckets[kOrderBuckets + kOrderBuckets - 1 - i] = sh[warp] + inc - v;
 }
 
+// Scatter in tiles of the block size: the tile's keys are counted in shared memory, each key
+// reserves its range of the bucket with one global atomic per tile, and every tracklet takes
+// its rank within the tile's range (an atomic on shared memory).  The order inside a bucket is
+// free, so no ordering between tiles is needed.
 __global__ void __launch_bounds__(256) k_order_scatter(const DevConst c, const Workspace w)
 {
+    __shared__ int cnt[kOrderBuckets];
+    __shared__ int base[kOrderBuckets];
     const int T = n_tracklets(w);
-    for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < T; t += gridDim.x * blockDim.x) {
-        const int pos = atomicAdd(&w.buckets[kOrderBuckets + work_key(c, w.starts[t].w)], 1);
-        if (TPC_IDX(pos, T, w.err, c, 4)) w.order[pos] = t;
+    for (int t0 = blockIdx.x * blockDim.x; t0 < T; t0 += gridDim.x * blockDim.x) {
+        for (int i = threadIdx.x; i < kOrderBuckets; i += blockDim.x) cnt[i] = 0;
+        __syncthreads();
+        const int t = t0 + threadIdx.x;
+        const int key = t < T ? work_key(c, w.starts[t].w) : 0;
+        const int rank = t < T ? atomicAdd(&cnt[key], 1) : 0;
+        __syncthreads();
+        for (int i = threadIdx.x; i < kOrderBuckets; i += blockDim.x)
+            if (cnt[i]) base[i] = atomicAdd(&w.buckets[kOrderBuckets + i], cnt[i]);
+        __syncthreads();
+        if (t < T) {
+            const int pos = base[key] + rank;
+            if (TPC_IDX(pos, T, w.err, c, 4)) w.order[pos] = t;
+        }
+        __syncthreads();
     }
 }
 

@@ -157,7 +157,7 @@ __global__ void __launch_bounds__(256) k_claim(const DevConst c, const Workspace
         if (key == 0ull) continue;
         const int n = w.tl_n[t];
         const int32_t *h = w.tl_hits + (int64_t)t * c.nr;
-        for (int i = lane; i < n; i += 32) atomicMax(&w.ckey[h[i]], key);
+        for (int i = lane; i < n; i += 32) atomicMax(&w.ckey[h[i]], key);   // result unused: no wait
     }
 }
 
