@@ -160,13 +160,15 @@ def construct_source_hash():
 
 
 def traffic_for_current_kernel():
+    """DRAM bytes and warp instructions of one k_construct launch from the committed ncu record,
+    or None when the kernel's sources changed since the capture."""
     if not os.path.exists(PROFILE_JSON):
-        return None, None
+        return None, None, None
     d = json.load(open(PROFILE_JSON))
     h = construct_source_hash()
     if d.get("source_sha256_16") != h:
-        return None, "kernel changed since capture"
-    return d.get("dram_bytes_per_launch"), d.get("note")
+        return None, None, "kernel changed since capture"
+    return d.get("dram_bytes_per_launch"), d.get("warp_instructions"), d.get("note")
 
 
 # ------------------------------------------------------------------------------------------------
@@ -451,13 +453,21 @@ def run_ours(args):
     cb = construct_bytes(stats)
     con_ms = mean_stage[4]
     achieved = cb / (con_ms * 1e-3) / 1e9
-    traffic, tnote = traffic_for_current_kernel()
+    traffic, winst, tnote = traffic_for_current_kernel()
     roof = {"kernel": "k_construct (A5 tracklet construction)", "bound": "hbm", "achieved": achieved,
             "peak": peak, "unit": "GB/s", "frac": achieved / peak, "peak_source": peak_kind + " (hbm_gbs)",
             "traffic": traffic, "algorithmic_bytes": cb, "launch_ms": con_ms,
             "timed_in": "timed region 2 (one event at a time)", "units": stats}
     if tnote:
         roof["traffic_note"] = tnote
+    if winst:
+        # the kernel is L2-resident and issue-bound: its warp instructions (ncu) over the launch time
+        # against the issue rate of 152 SMs x 4 schedulers at the sampled SM clock
+        sm_mhz = clk.get("sm_mhz") or 2070.0
+        issue_peak = 152 * 4 * sm_mhz * 1e6
+        roof["issue"] = {"achieved": winst / (con_ms * 1e-3), "peak": issue_peak, "unit": "warp instructions/s",
+                         "frac": winst / (con_ms * 1e-3) / issue_peak, "warp_instructions": winst,
+                         "peak_source": "152 SMs x 4 schedulers x sampled SM clock"}
     line = {"metric": METRIC, "value": value, "unit": "events/s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": 1e3 * total_s / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
