@@ -361,12 +361,13 @@ static size_t carve(tpc_tracker *tr, const WsSizes &s, Alloc &a)
         w.g_cov = a.take<float>(15 * s.T);
         w.g_x = a.take<float>(s.T);
         w.g_sec = a.take<int32_t>(s.T);
+        w.g_list = a.take<int32_t>(2 * s.T);
     } else {
         w.tl_opar = w.tl_ocov = w.tl_ox = w.g_chi = w.g_par = w.g_cov = w.g_x = nullptr;
         w.used = nullptr;
         w.gkey = nullptr;
         w.gent = nullptr;
-        w.gpool = w.g_off = w.g_n = w.g_own = w.g_sec = nullptr;
+        w.gpool = w.g_off = w.g_n = w.g_own = w.g_sec = w.g_list = nullptr;
         w.gpool_cap = 0;
     }
     if (tr->dc.merge) {

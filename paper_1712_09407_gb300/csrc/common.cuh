@@ -31,6 +31,7 @@ enum {
     CNT_GLIST = 8,      // global tracking: prolongations of the call (2 per tracklet)
     CNT_STRACKS = 9,    // merger: sector tracks (CNT_TRACKS then counts the merged tracks)
     CNT_SHITS = 10,     // merger: clusters of the sector tracks
+    CNT_GEDGE = 11,     // global tracking: prolongations past the edge test
     CNT_COUNT = 12
 };
 
@@ -109,6 +110,7 @@ struct Workspace {
     float *g_chi;          // [2 * tcap]
     float *g_par, *g_cov, *g_x;         // inward prolongation's last state [5|15|1][tcap]
     int32_t *g_sec;        // [tcap] sector (within the event) of that state
+    int32_t *g_list;       // [2 * tcap] prolongations past the edge test
     // track merger
     int32_t *in_sec;       // [input clusters] sector (index within the call)
     OutBuffers st;         // sector tracks (A7 output) when the merger runs after them

@@ -90,6 +90,23 @@ __device__ __forceinline__ bool pool_append(const DevConst &c, const Workspace &
     return true;
 }
 
+// Whether prolongation (end at x_end, row r_end, sector `sec`) leaves its sector at the next row in
+// direction dir and can be taken into the neighbour's frame (the first steps of prolong, which
+// repeats them).
+__device__ __forceinline__ bool crosses_edge(const DevConst &c, int sec, const KF &end, float x_end, int r_end,
+                                             int dir)
+{
+    const int rn = r_end + dir;
+    if (rn < 0 || rn >= c.nr) return false;
+    KF pr = end;
+    if (!propagate(pr, c.row_x[rn] - x_end, c)) return false;
+    if (!(fabsf(pr.p0) > c.row_x[rn] * c.th)) return false;
+    const bool plus = pr.p0 > 0.0f;
+    KF st = end;
+    float xs;
+    return rotate_state(st, x_end, c.c20, plus ? c.s20 : -c.s20, c, xs);
+}
+
 // One prolongation p = 2 t + d from `end` (at x_end, row r_end, sector `sec` of the call) in
 // direction dir.  Claims and records the clusters it finds; returns their number.
 __device__ int prolong(const DevConst &c, const Workspace &w, int p, int sec, const KF &end, float x_end, int r_end,
@@ -170,32 +187,57 @@ __global__ void __launch_bounds__(256) k_global_used(const DevConst c, const Wor
     }
 }
 
-// Every prolongation of every accepted track: clusters claimed and pooled, count, chi2, final
-// inward state.
-__global__ void __launch_bounds__(kGlobalBlock, 4) k_global_find(const DevConst c, const Workspace w)
+// Edge test of every prolongation of every accepted track; the ones that will search are listed
+// (warp-aggregated), so that the search kernel starts all of them at once.
+__global__ void __launch_bounds__(kGlobalBlock) k_global_edge(const DevConst c, const Workspace w)
 {
     const int T = n_tracklets(w);
-    const int tcap = (int)w.tcap;
-    for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < 2 * T; p += gridDim.x * blockDim.x) {
-        const int t = p >> 1, d = p & 1;
-        int n = 0;
-        float chi = 0.0f;
-        if (w.tl_inner[t] >= 0) {
-            KF end, fin;
-            float xe, xf;
-            int re, s2;
-            end_state(c, w, t, d, end, xe, re);
-            const int sec = w.starts[t].w >> 16;
-            n = prolong(c, w, p, sec, end, xe, re, d == 0 ? -1 : 1, prolong_key(w, t, d), chi, fin, xf, s2);
-            if (d == 0 && n > 0) {
-                store_state(w.g_par, w.g_cov, tcap, t, fin);
-                w.g_x[t] = xf;
-                w.g_sec[t] = s2;
+    const int lane = threadIdx.x & 31;
+    for (int p0 = blockIdx.x * blockDim.x; p0 < 2 * T; p0 += gridDim.x * blockDim.x) {
+        const int p = p0 + threadIdx.x;
+        bool go = false;
+        if (p < 2 * T) {
+            const int t = p >> 1, d = p & 1;
+            if (w.tl_inner[t] >= 0) {
+                KF end;
+                float xe;
+                int re;
+                end_state(c, w, t, d, end, xe, re);
+                go = crosses_edge(c, w.starts[t].w >> 16, end, xe, re, d == 0 ? -1 : 1);
             }
+            w.g_n[p] = 0;
+            w.g_chi[p] = 0.0f;
+            w.g_own[p] = 0;
+        }
+        const unsigned mask = __ballot_sync(kFull, go);
+        int base = 0;
+        if (lane == 0 && mask) base = atomicAdd(&w.counters[CNT_GEDGE], __popc(mask));
+        base = __shfl_sync(kFull, base, 0);
+        if (go) w.g_list[base + __popc(mask & lanemask_lt())] = p;
+    }
+}
+
+// The listed prolongations: clusters claimed and pooled, count, chi2, final inward state.
+__global__ void __launch_bounds__(kGlobalBlock, 4) k_global_find(const DevConst c, const Workspace w)
+{
+    const int L = w.counters[CNT_GEDGE];
+    const int tcap = (int)w.tcap;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < L; i += gridDim.x * blockDim.x) {
+        const int p = w.g_list[i];
+        const int t = p >> 1, d = p & 1;
+        KF end, fin;
+        float xe, xf, chi;
+        int re, s2;
+        end_state(c, w, t, d, end, xe, re);
+        const int sec = w.starts[t].w >> 16;
+        const int n = prolong(c, w, p, sec, end, xe, re, d == 0 ? -1 : 1, prolong_key(w, t, d), chi, fin, xf, s2);
+        if (d == 0 && n > 0) {
+            store_state(w.g_par, w.g_cov, tcap, t, fin);
+            w.g_x[t] = xf;
+            w.g_sec[t] = s2;
         }
         w.g_n[p] = n;
         w.g_chi[p] = chi;
-        w.g_own[p] = 0;
     }
 }
 
@@ -217,10 +259,11 @@ int launch_global(const DevConst &c, const Workspace &w, int64_t n_slots, const 
     cudaMemsetAsync(w.gkey, 0, (size_t)n_slots * sizeof(unsigned long long), s);
     const int grid = lc.num_sms * 8;
     k_global_used<<<grid, 256, 0, s>>>(c, w);
-    k_global_find<<<lc.num_sms * 32, kGlobalBlock, 0, s>>>(c, w);    // one round for 2 x 300 k tracklets
+    k_global_edge<<<lc.num_sms * 16, kGlobalBlock, 0, s>>>(c, w);
+    k_global_find<<<lc.num_sms * 4, kGlobalBlock, 0, s>>>(c, w);    // 78 k threads: every listed one starts at once
     const int scans = launch_scan_i32(w.g_n, w.g_off, 2 * w.tcap, w.counters + CNT_GLIST, w.scan_tmp, nullptr, s);
     k_global_place<<<grid, 256, 0, s>>>(w);
-    return 3 + scans;
+    return 4 + scans;
 }
 
 }  // namespace tpc
