@@ -121,6 +121,14 @@ typedef struct {
                                   (on a stream of the tracker's own) that updates the tracker's executable
                                   graph in place and is launched on the call's stream as one unit (default);
                                   0: plain stream launches.  Same work, same results. */
+    int seed_kernel;           /* -1: chosen by the call's size (default); 0: each constructor lane walks its
+                                  tracklet's chain for the seed when it takes the tracklet; 1: a separate
+                                  launch computes every seed first.  Same seeds, same results. */
+    int order_group;           /* cluster slots per group of the constructor's work order (a call with many
+                                  events builds one group's tracklets before the next group's, so that the
+                                  rows being searched stay in L2); 0: one group.  At most 6144 / kb groups
+                                  per call, kb = 2 n_rows + 2 rounded up to a multiple of 32 (19 groups for
+                                  159 rows; larger groups when the call holds more). */
 } tpc_tuning;
 
 typedef struct tpc_tracker tpc_tracker;

@@ -66,6 +66,7 @@ def tune(tracker: Tracker, y, z, row, counts, repeats: int = 3, stream=None, log
     search("neighbours_block", [64, 128, 256], ["neighbours"])
     search("construct_block", [64, 96, 128], ["construction"])
     search("construct_ctas_per_sm", [0, 4, 6, 8, 10, 12], ["construction"])
+    search("seed_kernel", [0, 1], ["construction"])
     search("use_graph", [0, 1], STAGES)
     tracker.set_tuning(best)
     return best

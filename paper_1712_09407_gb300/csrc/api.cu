@@ -181,6 +181,8 @@ extern "C" void tpc_tuning_default(tpc_tuning *t)
     t->stage_rows = 1;
     t->tracklet_capacity = 0;
     t->use_graph = 1;
+    t->seed_kernel = -1;
+    t->order_group = 3 << 20;
 }
 
 extern "C" const char *tpc_status_string(int s)
@@ -292,7 +294,8 @@ extern "C" int tpc_tracker_set_tuning(tpc_tracker *tr, const tpc_tuning *t)
     if (!(t->bin_occupancy >= 0.5f) || t->neighbours_block < 32 || t->neighbours_block > 256 ||
         t->neighbours_block % 32 || t->construct_block < 32 || t->construct_block > 128 ||
         t->construct_block % 32 || t->construct_ctas_per_sm < 0 || t->construct_mode < 0 || t->construct_mode > 1 ||
-        t->tracklet_capacity < 0 || t->use_graph < 0 || t->use_graph > 1)
+        t->tracklet_capacity < 0 || t->use_graph < 0 || t->use_graph > 1 || t->seed_kernel < -1 ||
+        t->seed_kernel > 1 || t->order_group < 0)
         return TPC_ERR_INVALID_ARG;
     tr->tuning = *t;
     return TPC_OK;
@@ -331,7 +334,8 @@ static size_t carve(tpc_tracker *tr, const WsSizes &s, Alloc &a)
     w.ckey = a.take<unsigned long long>(s.P);
     w.starts = a.take<int4>(s.T);
     w.order = a.take<int32_t>(s.T);
-    w.buckets = a.take<int32_t>(2 * kOrderBuckets);
+    w.seeds = a.take<float4>(2 * s.T);
+    w.buckets = a.take<int32_t>(2 * kOrderCursors);
     w.sw_sec = a.take<int32_t>(2 * (s.R / tr->n_rows) + 64);
     w.sw_chunks = a.take<int4>(s.T / 32 + s.R / tr->n_rows + 64);
     w.tl_n = a.take<int32_t>(s.T);
@@ -641,6 +645,10 @@ static int run(tpc_tracker *tr, const float *y, const float *z, const uint8_t *r
     lc.construct_mode = tr->tuning.construct_mode;
     lc.stage_rows = tr->tuning.stage_rows;
     lc.neighbours_smem_max = smem;
+    lc.seed_kernel = tr->tuning.seed_kernel;
+    lc.n_clusters = n_total;
+    lc.n_slots = s_off;
+    lc.order_group = tr->tuning.order_group;
 
     // The call's copies, clears and launches go to the caller's stream, or (graph mode) are
     // captured on the tracker's own stream into a graph that updates the cached executable graph

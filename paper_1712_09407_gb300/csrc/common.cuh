@@ -14,6 +14,8 @@ constexpr int kSlotAlign = 8;       // sorted row segments start on 8-element (3
 constexpr int kCellAlign = 4;       // cell-start segments start on 16 B boundaries
 constexpr unsigned kFull = 0xffffffffu;
 constexpr int kOrderBuckets = 512;  // >= 2 * kMaxRows + 2 (expected-work keys)
+constexpr int kOrderCursors = 6144; // buckets of the constructor's grouped order (the scatter holds two
+                                    // arrays of them in 48 KB of shared memory); cursors follow them
 
 // Error word layout in the workspace: [0] status, [1] event, [2] sector, [3] stage.
 enum { ERR_STATUS = 0, ERR_EVENT = 1, ERR_SECTOR = 2, ERR_STAGE = 3 };
@@ -87,8 +89,10 @@ struct Workspace {
     unsigned long long *ckey;   // A6 claims
     // per tracklet
     int4 *starts;          // {first, -1, -1, (sector << 16) | (chain length up to max(4, min_chain) << 8) | row}
-    int32_t *order;        // tracklets in the order the constructor takes them (longest expected first)
-    int32_t *buckets;      // [kOrderBuckets * 2] histogram / cursors of the ordering sort
+    int32_t *order;        // tracklets in the order the sweep constructor takes them
+    float4 *seeds;         // [2 * tcap] per work-queue position: {p0, p1, p2, p3}, {p4, tracklet (-1 - t if
+                           // the seed failed), packed start word, input index of the start cluster}
+    int32_t *buckets;      // [2 * kOrderCursors] histogram / cursors of the ordering sort
     int32_t *sw_sec;       // [2 * sectors] tracklets per sector, scatter cursors (sweep constructor)
     int4 *sw_chunks;       // {sector, first position in order, count, 0} per chunk (sweep constructor)
     int32_t *tl_n;
@@ -239,6 +243,10 @@ struct LaunchCfg {
     int construct_mode;        // 0: per-lane work queue, 1: sector sweep
     int stage_rows;
     int neighbours_smem_max;   // bytes of dynamic shared memory for staged rows
+    int seed_kernel;           // -1: by the call's size, 0: seeds walked by the constructor, 1: k_seed
+    int64_t n_clusters;        // clusters in the call
+    int64_t n_slots;           // cluster slots in the call (rows padded)
+    int64_t order_group;       // slots per group of the constructor's order (0: one group)
 };
 int launch_ingest(const DevConst &c, const Workspace &w, const float *y, const float *z, const uint8_t *row,
                    int64_t R, cudaStream_t s);

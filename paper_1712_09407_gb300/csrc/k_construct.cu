@@ -19,8 +19,11 @@ namespace tpc {
 // work queue hands out the long tracklets first and ends on short ones.  A chain of 4 or more
 // clusters usually belongs to a real track, which runs outwards from its start row to the last
 // row and back to row 0: about 2 * n_rows - start row visits.  Shorter chains are mostly noise
-// triplets that stop after a few rows.  The order only changes which lane builds which
-// tracklet when; every tracklet's result is the same.
+// triplets that stop after a few rows.  In a call with many events the tracklets are first
+// grouped by the slot of their start cluster (groups of gslots consecutive slots, a few
+// central-like events): the queue finishes one group's tracklets before the next group's, so
+// the rows the resident lanes search stay in L2.  The order only changes which lane builds
+// which tracklet when; every tracklet's result is the same.
 // ---------------------------------------------------------------------------------------------
 __device__ __forceinline__ int work_key(const DevConst &c, int packed)
 {
@@ -28,57 +31,73 @@ __device__ __forceinline__ int work_key(const DevConst &c, int packed)
     return len >= 4 ? 2 * c.nr - r0 + 1 : 0;       // 0 .. 2 nr + 1 < kOrderBuckets
 }
 
-__global__ void __launch_bounds__(256) k_order_hist(const DevConst c, const Workspace w)
+// Buckets per group: the work keys 0 .. 2 nr + 1, rounded up to a multiple of 32.
+__host__ __device__ __forceinline__ int order_kb(int nr) { return (2 * nr + 2 + 31) / 32 * 32; }
+
+// Bucket of a tracklet: ascending group, then descending work key.
+__device__ __forceinline__ int work_bucket(const DevConst &c, int4 sd, int gslots)
 {
-    __shared__ int h[kOrderBuckets];
-    for (int i = threadIdx.x; i < kOrderBuckets; i += blockDim.x) h[i] = 0;
+    const int kb = order_kb(c.nr);
+    return (sd.x / gslots) * kb + (kb - 1 - work_key(c, sd.w));
+}
+
+__global__ void __launch_bounds__(256) k_order_hist(const DevConst c, const Workspace w, int gslots, int nb)
+{
+    extern __shared__ int h[];
+    for (int i = threadIdx.x; i < nb; i += blockDim.x) h[i] = 0;
     __syncthreads();
     const int T = n_tracklets(w);
     for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < T; t += gridDim.x * blockDim.x)
-        atomicAdd(&h[work_key(c, w.starts[t].w)], 1);
+        atomicAdd(&h[work_bucket(c, w.starts[t], gslots)], 1);
     __syncthreads();
-    for (int i = threadIdx.x; i < kOrderBuckets; i += blockDim.x)
+    for (int i = threadIdx.x; i < nb; i += blockDim.x)
         if (h[i]) atomicAdd(&w.buckets[i], h[i]);
 }
 
-// Exclusive scan of the buckets in descending key order; the cursors start at the offsets.
-__global__ void __launch_bounds__(kOrderBuckets) k_order_scan(const Workspace w)
+// Exclusive scan of the nb buckets (one CTA, a contiguous run of buckets per thread); the
+// cursors (at kOrderCursors) start at the offsets.
+__global__ void __launch_bounds__(1024) k_order_scan(const Workspace w, int nb)
 {
-    __shared__ int sh[kOrderBuckets / 32 + 1];
-    const int i = threadIdx.x;                      // bucket kOrderBuckets - 1 - i
-    const int v = w.buckets[kOrderBuckets - 1 - i];
-    const int lane = i & 31, warp = i >> 5;
-    const int inc = warp_incl_scan(v);
+    __shared__ int sh[32];
+    const int per = (nb + 1023) / 1024, i0 = threadIdx.x * per;
+    const int i1 = i0 + per < nb ? i0 + per : nb;
+    int sum = 0;
+    for (int i = i0; i < i1; i++) sum += w.buckets[i];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int inc = warp_incl_scan(sum);
     if (lane == 31) sh[warp] = inc;
     __syncthreads();
     if (warp == 0) {
-        const int nw = kOrderBuckets / 32;
-        const int x = lane < nw ? sh[lane] : 0;
-        const int xi = warp_incl_scan(x);
-        if (lane < nw) sh[lane] = xi - x;
+        const int x = sh[lane];
+        sh[lane] = warp_incl_scan(x) - x;
     }
     __syncthreads();
-    w.buckets[kOrderBuckets + kOrderBuckets - 1 - i] = sh[warp] + inc - v;
+    int run = sh[warp] + inc - sum;
+    for (int i = i0; i < i1; i++) {
+        const int v = w.buckets[i];
+        w.buckets[kOrderCursors + i] = run;
+        run += v;
+    }
 }
 
-// Scatter in tiles of the block size: the tile's keys are counted in shared memory, each key
-// reserves its range of the bucket with one global atomic per tile, and every tracklet takes
-// its rank within the tile's range (an atomic on shared memory).  The order inside a bucket is
-// free, so no ordering between tiles is needed.
-__global__ void __launch_bounds__(256) k_order_scatter(const DevConst c, const Workspace w)
+// Scatter in tiles of the block size: the tile's buckets are counted in shared memory, each
+// bucket reserves its range with one global atomic per tile, and every tracklet takes its rank
+// within the tile's range (an atomic on shared memory).  The order inside a bucket is free, so
+// no ordering between tiles is needed.
+__global__ void __launch_bounds__(256) k_order_scatter(const DevConst c, const Workspace w, int gslots, int nb)
 {
-    __shared__ int cnt[kOrderBuckets];
-    __shared__ int base[kOrderBuckets];
+    extern __shared__ int sm[];
+    int *cnt = sm, *base = sm + nb;
     const int T = n_tracklets(w);
     for (int t0 = blockIdx.x * blockDim.x; t0 < T; t0 += gridDim.x * blockDim.x) {
-        for (int i = threadIdx.x; i < kOrderBuckets; i += blockDim.x) cnt[i] = 0;
+        for (int i = threadIdx.x; i < nb; i += blockDim.x) cnt[i] = 0;
         __syncthreads();
         const int t = t0 + threadIdx.x;
-        const int key = t < T ? work_key(c, w.starts[t].w) : 0;
+        const int key = t < T ? work_bucket(c, w.starts[t], gslots) : 0;
         const int rank = t < T ? atomicAdd(&cnt[key], 1) : 0;
         __syncthreads();
-        for (int i = threadIdx.x; i < kOrderBuckets; i += blockDim.x)
-            if (cnt[i]) base[i] = atomicAdd(&w.buckets[kOrderBuckets + i], cnt[i]);
+        for (int i = threadIdx.x; i < nb; i += blockDim.x)
+            if (cnt[i]) base[i] = atomicAdd(&w.buckets[kOrderCursors + i], cnt[i]);
         __syncthreads();
         if (t < T) {
             const int pos = base[key] + rank;
@@ -88,10 +107,34 @@ __global__ void __launch_bounds__(256) k_order_scatter(const DevConst c, const W
     }
 }
 
+// Seed of every tracklet, written at its work-queue position: the walk along the chain and the
+// three-point circle run here, one thread per tracklet with the latency of the chain's dependent
+// loads hidden by occupancy, so that a constructor lane starting a tracklet reads one 32 B record
+// instead of stalling its whole warp on the walk.
+__global__ void __launch_bounds__(256) k_seed(const DevConst c, const Workspace w)
+{
+    const int T = n_tracklets(w);
+    for (int q = blockIdx.x * blockDim.x + threadIdx.x; q < T; q += gridDim.x * blockDim.x) {
+        const int t = w.order[q];
+        if (!TPC_IDX(t, T, w.err, c, 4)) continue;
+        const int4 sd = w.starts[t];
+        KF st{};
+        const bool ok = seed_tracklet(c, w, sd, st);
+        w.tl_n[t] = 0;
+        w.tl_key[t] = 0ull;
+        w.seeds[2 * q] = make_float4(st.p0, st.p1, st.p2, st.p3);
+        w.seeds[2 * q + 1] = make_float4(st.p4, __int_as_float(ok ? t : -1 - t), __int_as_float(sd.w),
+                                         __int_as_float(w.orig[sd.x]));
+    }
+}
+
 // 128 threads and 6 resident CTAs per SM: 80 registers without spills (measured fastest).
 // GLOBAL: also store the outward pass's final state (the outer end for global tracking); a
 // separate instance so that the plain tracker keeps its register allocation.
-template <bool GLOBAL>
+// PRESEED: seeds come from k_seed's records (many tracklets per lane); otherwise each lane walks
+// its tracklet's chain when it takes the tracklet (few tracklets per lane, where a separate seed
+// launch costs more than the walks it saves).
+template <bool GLOBAL, bool PRESEED>
 __global__ void __launch_bounds__(128, 6)
 k_construct(const DevConst c, const Workspace w)
 {
@@ -105,14 +148,31 @@ k_construct(const DevConst c, const Workspace w)
         if (phase == 0) {
             const int q = atomicAdd(&w.counters[CNT_QUEUE], 1);
             if (q >= T) break;
-            t = w.order[q];
-            const int4 sd = w.starts[t];
-            sec = sd.w >> 16;
-            const int r0 = sd.w & 0xff;
-            orig0 = w.orig[sd.x];
-            w.tl_n[t] = 0;
-            w.tl_key[t] = 0ull;
-            if (!seed_tracklet(c, w, sd, st)) continue;
+            int r0;
+            if (PRESEED) {
+                const float4 sa = w.seeds[2 * q], sb = w.seeds[2 * q + 1];
+                t = __float_as_int(sb.y);
+                if (t < 0) continue;                     // unusable seed: the tracklet stays empty
+                const int packed = __float_as_int(sb.z);
+                sec = packed >> 16;
+                r0 = packed & 0xff;
+                orig0 = __float_as_int(sb.w);
+                st.p0 = sa.x;
+                st.p1 = sa.y;
+                st.p2 = sa.z;
+                st.p3 = sa.w;
+                st.p4 = sb.x;
+                set_seed_cov(st, c);
+            } else {
+                t = w.order[q];
+                const int4 sd = w.starts[t];
+                sec = sd.w >> 16;
+                r0 = sd.w & 0xff;
+                orig0 = w.orig[sd.x];
+                w.tl_n[t] = 0;
+                w.tl_key[t] = 0ull;
+                if (!seed_tracklet(c, w, sd, st)) continue;
+            }
             phase = 1;
             r = r0;
             xs = c.row_x[r0];
@@ -197,20 +257,36 @@ int launch_construct(const DevConst &c, const Workspace &w, const LaunchCfg &lc,
     int per_sm = lc.construct_ctas_per_sm;
     if (per_sm <= 0) {
         int occ = 0;
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, c.global ? k_construct<true> : k_construct<false>,
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, c.global ? k_construct<true, false> : k_construct<false, false>,
                                                       lc.construct_block, 0);
         per_sm = occ > 0 ? occ : 1;
     }
-    cudaMemsetAsync(w.buckets, 0, kOrderBuckets * sizeof(int32_t), s);
+    // seed kernel when the call is expected to give each resident lane several tracklets (about one
+    // start hit per 20 clusters in central-like events; 6 resident CTAs per SM)
+    const int64_t lanes = (int64_t)lc.num_sms * 6 * lc.construct_block;
+    const bool preseed = lc.seed_kernel > 0 || (lc.seed_kernel < 0 && lc.n_clusters / 20 > 4 * lanes);
+    // groups of order_group slots, as many as the histogram's kOrderCursors buckets hold
+    const int kb = order_kb(c.nr), max_groups = kOrderCursors / kb;
+    int64_t gs = lc.order_group > 0 ? lc.order_group : lc.n_slots + 1;
+    if ((lc.n_slots + gs - 1) / gs > max_groups) gs = (lc.n_slots + max_groups - 1) / max_groups;
+    if (gs < 1) gs = 1;
+    const int ng = (int)((lc.n_slots + gs - 1) / gs) > 0 ? (int)((lc.n_slots + gs - 1) / gs) : 1;
+    const int nb = ng * kb;
+    cudaMemsetAsync(w.buckets, 0, nb * sizeof(int32_t), s);
     const int og = lc.num_sms * 2;
-    k_order_hist<<<og, 256, 0, s>>>(c, w);
-    k_order_scan<<<1, kOrderBuckets, 0, s>>>(w);
-    k_order_scatter<<<og, 256, 0, s>>>(c, w);
-    if (c.global)
-        k_construct<true><<<lc.num_sms * per_sm, lc.construct_block, 0, s>>>(c, w);
-    else
-        k_construct<false><<<lc.num_sms * per_sm, lc.construct_block, 0, s>>>(c, w);
-    return 4;
+    k_order_hist<<<og, 256, nb * sizeof(int), s>>>(c, w, (int)gs, nb);
+    k_order_scan<<<1, 1024, 0, s>>>(w, nb);
+    k_order_scatter<<<og, 256, 2 * nb * sizeof(int), s>>>(c, w, (int)gs, nb);
+    if (preseed) k_seed<<<lc.num_sms * 8, 256, 0, s>>>(c, w);
+    const unsigned grid = lc.num_sms * per_sm;
+    if (c.global) {
+        if (preseed) k_construct<true, true><<<grid, lc.construct_block, 0, s>>>(c, w);
+        else k_construct<true, false><<<grid, lc.construct_block, 0, s>>>(c, w);
+    } else {
+        if (preseed) k_construct<false, true><<<grid, lc.construct_block, 0, s>>>(c, w);
+        else k_construct<false, false><<<grid, lc.construct_block, 0, s>>>(c, w);
+    }
+    return preseed ? 5 : 4;
 }
 
 }  // namespace tpc

@@ -368,13 +368,14 @@ __device__ __forceinline__ bool rotate_state(KF &s, float x, float cd, float sd,
 __device__ __forceinline__ bool seed_tracklet(const DevConst &c, const Workspace &w, int4 sd, KF &st)
 {
     const int r0 = sd.w & 0xff;
-    int len = 1, last = sd.x;
+    // one pass over the chain: the middle cluster (index (len - 1) / 2) advances on every second
+    // link, its load independent of the walk's own chain of loads
+    int len = 1, last = sd.x, mid = sd.x;
     for (int nx = w.up[last]; nx >= 0 && len < c.nr; nx = w.up[nx]) {
         last = nx;
         len++;
+        if (len & 1) mid = w.up[mid];
     }
-    int mid = sd.x;
-    for (int k = 0; k < (len - 1) / 2; k++) mid = w.up[mid];
     const float2 q0 = w.yz[sd.x], q1 = w.yz[mid], q2 = w.yz[last];
     const float x3[3] = {c.row_x[r0], c.row_x[r0 + (len - 1) / 2], c.row_x[r0 + len - 1]};
     const float y3[3] = {q0.x, q1.x, q2.x};

@@ -46,7 +46,8 @@ class tpc_params(ctypes.Structure):
 class tpc_tuning(ctypes.Structure):
     _fields_ = [("bin_occupancy", c_float), ("neighbours_block", c_int), ("construct_block", c_int),
                 ("construct_ctas_per_sm", c_int), ("construct_mode", c_int), ("stage_rows", c_int),
-                ("tracklet_capacity", c_int), ("use_graph", c_int)]
+                ("tracklet_capacity", c_int), ("use_graph", c_int), ("seed_kernel", c_int),
+                ("order_group", c_int)]
 
 
 class tpc_track_view(ctypes.Structure):

@@ -251,7 +251,9 @@ def test_noisy_sector():
     dict(bin_occupancy=0.5), dict(bin_occupancy=16.0), dict(stage_rows=0),
     dict(neighbours_block=64, construct_block=64), dict(construct_block=96, construct_ctas_per_sm=1),
     dict(bin_occupancy=2.0, neighbours_block=128, construct_ctas_per_sm=0), dict(construct_mode=1),
-    dict(construct_mode=1, bin_occupancy=4.0), dict(use_graph=0), dict(use_graph=0, construct_mode=1)])
+    dict(construct_mode=1, bin_occupancy=4.0), dict(use_graph=0), dict(use_graph=0, construct_mode=1),
+    dict(seed_kernel=1), dict(seed_kernel=1, construct_ctas_per_sm=1), dict(seed_kernel=0),
+    dict(order_group=4096), dict(order_group=0, seed_kernel=1), dict(order_group=1)])
 def test_tuning_does_not_change_results(tuning):
     """Grid bin size, block shapes and staging only change speed (the autotuner relies on it)."""
     ev = _small36()

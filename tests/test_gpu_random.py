@@ -1,8 +1,8 @@
 """Randomised parity: seeded small events of varied recipes (multiplicity, secondaries, pT cut, noise,
 eta range) tracked with varied readings of the open points (chi2 gate, window width, miss limit,
-chain length, minimum clusters, alpha) and the optional stages switched at random.  The CUDA path
-and the float oracle evaluate the same operations, so every case must be identical: the same tracks
-with the same clusters and bit-identical parameters."""
+chain length, minimum clusters, alpha), the optional stages and the seed launch switched at random.
+The CUDA path and the float oracle evaluate the same operations, so every case must be identical:
+the same tracks with the same clusters and bit-identical parameters."""
 import numpy as np
 import pytest
 import torch
@@ -26,12 +26,13 @@ def _case(k):
                     max_miss=int(rng.choice([3, 10])), min_chain=int(rng.choice([3, 4])),
                     min_clusters=int(rng.choice([20, 30])), alpha=float(rng.choice([2.0, 6.0])))
     flags = dict(global_tracking=bool(rng.integers(0, 2)), merge=bool(rng.integers(0, 2)))
-    return spec, readings, flags
+    tuning = dict(seed_kernel=int(rng.integers(0, 2)), order_group=int(rng.choice([0, 4096, 4 << 20])))
+    return spec, readings, flags, tuning
 
 
 @pytest.mark.parametrize("k", range(CASES))
 def test_random_case_equals_oracle(k):
-    spec, readings, flags = _case(k)
+    spec, readings, flags, tuning = _case(k)
     ev = eventgen.generate_event(spec, eventgen.Geometry(), seed=77, event=k)
     ref = oracle.track_event(oracle.config_for(ev.geometry, **readings, **flags), ev.y, ev.z, ev.row, ev.counts,
                              precision=32)
@@ -39,6 +40,7 @@ def test_random_case_equals_oracle(k):
     for name, v in readings.items():
         setattr(p, name, v)
     tr = Tracker.for_geometry(ev.geometry, params=p, **flags)
+    tr.set_tuning(tuning)
     r = tr.track(*(torch.from_numpy(a).cuda() for a in (ev.y, ev.z, ev.row)), ev.counts)
     out = r.to_numpy()
     r.release()
@@ -49,7 +51,7 @@ def test_random_case_equals_oracle(k):
     else:
         first, nhits, hits, par, cov, x = ref.trk_first, ref.trk_nhits, ref.trk_hits, ref.trk_par, ref.trk_cov, ref.trk_x
         chi2, ndf, sector = ref.trk_chi2, ref.trk_ndf, ref.trk_sector
-    print(k, ev.n, readings, flags, len(nhits), "tracks")
+    print(k, ev.n, readings, flags, tuning, len(nhits), "tracks")
     assert np.array_equal(out["nhits"], nhits) and np.array_equal(out["first"], first)
     assert np.array_equal(out["hits"], hits)
     assert np.array_equal(out["ndf"], ndf) and np.array_equal(out["sector"], sector)
