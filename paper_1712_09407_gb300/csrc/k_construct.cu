@@ -131,9 +131,10 @@ __global__ void __launch_bounds__(256) k_seed(const DevConst c, const Workspace 
 // 128 threads and 6 resident CTAs per SM: 80 registers without spills (measured fastest).
 // GLOBAL: also store the outward pass's final state (the outer end for global tracking); a
 // separate instance so that the plain tracker keeps its register allocation.
-// PRESEED: seeds come from k_seed's records (many tracklets per lane); otherwise each lane walks
-// its tracklet's chain when it takes the tracklet (few tracklets per lane, where a separate seed
-// launch costs more than the walks it saves).
+// PRESEED: seeds come from k_seed's records and the row search runs as one flat loop (many
+// tracklets per lane: throughput-bound); otherwise each lane walks its tracklet's chain when it
+// takes the tracklet and the row search runs as nested loops (few tracklets per lane, where the
+// latency of the last long tracklets decides the time).
 template <bool GLOBAL, bool PRESEED>
 __global__ void __launch_bounds__(128, 6)
 k_construct(const DevConst c, const Workspace w)
@@ -196,7 +197,7 @@ k_construct(const DevConst c, const Workspace w)
             const Gain g = residual_cov_inv(pr, c);
             float chi2 = 0.0f;
             float2 q_unused;      // reloaded below instead: keeping it live costs spills at 80 registers
-            const int bl = search_cells(c, w.yz + rg.x, w.orig + rg.x, w.cell + rg.y, gr, rg.z, rg.w, pr, g, chi2,
+            const int bl = search_cells<PRESEED>(c, w.yz + rg.x, w.orig + rg.x, w.cell + rg.y, gr, rg.z, rg.w, pr, g, chi2,
                                         q_unused, cands);
             const int b = bl < 0 ? -1 : rg.x + bl;
             if (b >= 0 && chi2 <= c.chi2max) {

@@ -211,11 +211,44 @@ __device__ __forceinline__ bool seed3(const float x[3], const float y[3], const 
     return true;
 }
 
+// Running minimum of a row search: the lowest chi2, ties to the lower input index.
+struct BestCand {
+    int best = -1, borig = -1;       // borig: input index of the best slot, loaded on the first tie
+    float bc = 0.0f;
+    float2 bq = make_float2(0.0f, 0.0f);
+
+    __device__ __forceinline__ void offer(int k, float2 q, float x2, const int32_t *orig)
+    {
+        if (best < 0 || x2 < bc) {
+            best = k;
+            bc = x2;
+            bq = q;
+            borig = -1;
+        } else if (x2 == bc) {
+            if (borig < 0) borig = orig[best];
+            const int o = orig[k];
+            if (o < borig) {
+                best = k;
+                bq = q;
+                borig = o;
+            }
+        }
+    }
+};
+
 // Best cluster of one row for a predicted state: minimum chi2 inside the window, ties to the
 // lower input index.  yz, orig, cell point at the row's slots and cell starts (global memory or a
 // shared-memory copy); gr = {ymin, zmin, 1/dy, 1/dz}, ny, nz its grid.  Returns the slot index
 // within the row, or -1; the best cluster's (y, z) in best_yz.  used (optional): clusters with a
 // nonzero byte are skipped.
+//
+// FLAT selects the loop shape; both visit the same candidates in the same order (cell rows iz
+// ascending, slots ascending), so the result is the same.  Nested loops (a loop per cell row)
+// keep one lane's search short, which matters when few warps are left to hide latency.  The flat
+// loop (an iteration either moves to the next cell row or tests one candidate) lets a warp run as
+// many iterations as its busiest lane has candidates plus cell rows instead of the sum over cell
+// rows of the busiest lane in each, which matters when the constructor is throughput-bound.
+template <bool FLAT = false>
 __device__ __forceinline__ int search_cells(const DevConst &c, const float2 *yz, const int32_t *orig,
                                             const int32_t *cell, const float4 gr, int ny, int nz, const KF &pr,
                                             const Gain &g, float &chi2_out, float2 &best_yz, int &ncand,
@@ -228,6 +261,27 @@ __device__ __forceinline__ int search_cells(const DevConst &c, const float2 *yz,
     const int iy1 = cell1(y + wy + kBinSlack, gr.x, gr.z, ny);
     const int iz0 = cell1(z - wz - kBinSlack, gr.y, gr.w, nz);
     const int iz1 = cell1(z + wz + kBinSlack, gr.y, gr.w, nz);
+    if (FLAT) {
+        BestCand b;
+        int iz = iz0 - 1, j = 0, e = 0;
+        while (true) {
+            if (j >= e) {
+                if (++iz > iz1) break;
+                j = cell[iz * ny + iy0];
+                e = cell[iz * ny + iy1 + 1];
+                ncand += e - j;
+                continue;
+            }
+            const int k = j++;
+            const float2 q = yz[k];                     // issued together with the used[] load
+            if (used && used[k]) continue;
+            if (!(fabsf(q.x - y) <= wy && fabsf(q.y - z) <= wz)) continue;
+            b.offer(k, q, chi2_of(g, q.x - y, q.y - z), orig);
+        }
+        chi2_out = b.bc;
+        best_yz = b.bq;
+        return b.best;
+    }
     int best = -1, borig = -1;       // borig: input index of the best slot, loaded on the first tie
     float bc = 0.0f;
     float2 bq = make_float2(0.0f, 0.0f);
@@ -239,7 +293,7 @@ __device__ __forceinline__ int search_cells(const DevConst &c, const float2 *yz,
             if (used && used[j]) continue;
             if (!(fabsf(q.x - y) <= wy && fabsf(q.y - z) <= wz)) continue;
             const float x2 = chi2_of(g, q.x - y, q.y - z);
-            if (best < 0 || x2 < bc) {
+            if (best < 0 || x2 < bc) {                  // the same rule as BestCand::offer
                 best = j;
                 bc = x2;
                 bq = q;
