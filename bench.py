@@ -1,12 +1,20 @@
 #!/usr/bin/env python
 """Throughput of the CUDA TPC sector tracker on the central-like workload.
 
-One step = one central-like event (16000 primaries + 3000 secondaries, 20 % noise, 36
+The workload is the central-like event (16000 primaries + 3000 secondaries, 20 % noise, 36
 sectors x 159 rows, about 3.3 M clusters) through every stage of the hot path: ingest and
 per-row grids, neighbours finder, evolution and start hits, tracklet construction,
-selection, output in canonical order.  Inputs are resident in HBM before the timed region;
-L2 is flushed (512 MB write, not timed) before every step; each step is timed with CUDA
-events on the tracker's stream and the step times are summed.
+selection, output in canonical order.
+
+value: one step = one call tracking --events-per-call (3) central-like events in one pass
+of every stage (tpc_track_batch); --inflight (2) calls are on the device at once, each on
+its own tracker and stream, as a stream of events is served.  Inputs (12 distinct events,
+more than L2 together) are resident in HBM before the timed region, which is bracketed by
+CUDA events on the streams; value = events / device time.  Beside it in the same line:
+the same stream with one event per call, one event at a time with L2 flushed before each
+(latency, per-stage times and the constructor's roofline), the optional stages, and the
+end-to-end figure from pinned host buffers through tpc_track_batch_host with the results
+copied back.
 
 Prints one JSON line (rank 0).  ``--impl reference`` times the CPU oracle (the reference
 arm of this build) on the host cores instead.
@@ -47,8 +55,10 @@ def parse():
     ap.add_argument("--workload", default="central", choices=["central", "batch"],
                     help="central: the metric's workload (default); batch: 64 events per call vs one at a time")
     ap.add_argument("--batch-events", type=int, default=64)
-    ap.add_argument("--inflight", type=int, default=2, help="central events on the device at once (one stream each)")
-    ap.add_argument("--resident", type=int, default=8, help="distinct resident central events (> L2 together)")
+    ap.add_argument("--inflight", type=int, default=2, help="tracker calls on the device at once (one stream each)")
+    ap.add_argument("--events-per-call", type=int, default=3,
+                    help="central events tracked by one call (tpc_track_batch); a step is one call")
+    ap.add_argument("--resident", type=int, default=12, help="distinct resident central events (> L2 together)")
     return ap.parse_args()
 
 
@@ -200,14 +210,17 @@ def run_reference(args):
     cfg = oracle.config_for(ev.geometry)
     for _ in range(args.warmup):
         oracle.track_event(cfg, ev.y, ev.z, ev.row, ev.counts, precision=32)
+    # at most --steps events and about a minute of CPU time
     t0 = time.perf_counter()
-    for _ in range(args.steps):
+    steps = 0
+    while steps < args.steps and (steps == 0 or time.perf_counter() - t0 < 60.0):
         oracle.track_event(cfg, ev.y, ev.z, ev.row, ev.counts, precision=32)
+        steps += 1
     dt = time.perf_counter() - t0
-    v = args.steps / dt
+    v = steps / dt
     cores = os.cpu_count()
     line = {"impl": "reference", "metric": METRIC, "value": v, "unit": "events/s", "n_gpus": args.gpus,
-            "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt * 1e3 / args.steps,
+            "steps": steps, "warmup": args.warmup, "ms_per_step": dt * 1e3 / steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
             "data": "synthetic", "config": {"workload": WORKLOAD, "clusters_per_event": ev.n},
             "cpu_baseline": {"value": v, "unit": "events/s", "cores": cores, "kind": "oracle",
@@ -244,18 +257,37 @@ def run_ours(args):
                                row=pool[0][2].numpy(), counts=pool[0][3], n=pool[0][4])   # first resident event
     dev = [(p[0].cuda(), p[1].cuda(), p[2].cuda(), p[3], p[4]) for p in pool]
     n_mean = float(np.mean([p[4] for p in pool]))
+    # calls of B consecutive resident events (inputs concatenated on the device and, for the
+    # end-to-end leg, in pinned host memory, before any timing)
+    B = max(1, args.events_per_call)
+    calls = []
+    for j in range(max(1, len(pool) // B)):
+        ps = [pool[(j * B + i) % len(pool)] for i in range(B)]
+        ds = [dev[(j * B + i) % len(dev)] for i in range(B)]
+        calls.append(dict(y=torch.cat([d[0] for d in ds]), z=torch.cat([d[1] for d in ds]),
+                          row=torch.cat([d[2] for d in ds]), counts=np.concatenate([p[3] for p in ps]),
+                          n=sum(p[4] for p in ps), hy=torch.cat([p[0] for p in ps]).pin_memory(),
+                          hz=torch.cat([p[1] for p in ps]).pin_memory(), hr=torch.cat([p[2] for p in ps]).pin_memory()))
     trackers = [Tracker.for_geometry(ev.geometry) for _ in range(args.inflight)]
     for t in trackers:
-        t.reserve(max(p[4] for p in pool), 1)
+        t.reserve(max(c_["n"] for c_ in calls), B)
     tr = trackers[0]
     streams = [torch.cuda.Stream() for _ in range(args.inflight)]
     stream = streams[0]
     flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
     torch.cuda.synchronize()
 
+    def call(t, c_, s_):
+        if B == 1:
+            return t.track(c_["y"], c_["z"], c_["row"], c_["counts"], stream=s_)
+        return t.track_batch(c_["y"], c_["z"], c_["row"], c_["counts"], B, stream=s_)
+
     for i, t in enumerate(trackers):
         with torch.cuda.stream(streams[i]):
             for k in range(args.warmup):
+                r = call(t, calls[k % len(calls)], streams[i])
+                r.sync()
+                r.release()
                 d = dev[k % len(dev)]
                 r = t.track(d[0], d[1], d[2], d[3], stream=streams[i])
                 r.sync()
@@ -267,8 +299,9 @@ def run_ours(args):
             torch.distributed.barrier()
         torch.cuda.synchronize()
 
-    # ---- timed region 1 (the value): a stream of central-like events, `inflight` of them on the
-    # device at once (one tracker and stream each), inputs larger than L2 so no flush is needed
+    # ---- timed region 1 (the value): a stream of calls of B central-like events each, `inflight`
+    # calls on the device at once (one tracker and stream each), inputs larger than L2 so no flush
+    # is needed
     for t in trackers:
         t.set_timing(True)
     clocks = ClockSampler(local)
@@ -293,9 +326,8 @@ def run_ours(args):
 
     for k in range(args.steps):
         i = k % args.inflight
-        d = dev[k % len(dev)]
         with torch.cuda.stream(streams[i]):
-            results.append(trackers[i].track(d[0], d[1], d[2], d[3], stream=streams[i]))
+            results.append(call(trackers[i], calls[k % len(calls)], streams[i]))
         if len(results) > 4 * args.inflight:
             retire(results.popleft())
     for e, s_ in zip(t_ends, streams):
@@ -306,7 +338,36 @@ def run_ours(args):
     while results:
         retire(results.popleft())
     total_s = reduce_max(max(t_start.elapsed_time(e) for e in t_ends) / 1e3, world, "cuda")
-    value = replica_throughput(total_s, args.steps, world)
+    value = replica_throughput(total_s, args.steps * B, world)
+
+    # the same stream with one event per call (tpc_track_event), for comparison
+    n_one = min(args.steps * B, 400)
+    o_start = torch.cuda.Event(enable_timing=True)
+    o_ends = [torch.cuda.Event(enable_timing=True) for _ in streams]
+    barrier()
+    o_start.record(streams[0])
+    for s_ in streams[1:]:
+        s_.wait_event(o_start)
+    pend = collections.deque()
+    for k in range(n_one):
+        i = k % args.inflight
+        d = dev[k % len(dev)]
+        with torch.cuda.stream(streams[i]):
+            pend.append(trackers[i].track(d[0], d[1], d[2], d[3], stream=streams[i]))
+        if len(pend) > 4 * args.inflight:
+            r = pend.popleft()
+            r.sync()
+            r.release()
+    for e, s_ in zip(o_ends, streams):
+        e.record(s_)
+    barrier()
+    while pend:
+        r = pend.popleft()
+        r.sync()
+        r.release()
+    one_call_s = reduce_max(max(o_start.elapsed_time(e) for e in o_ends) / 1e3, world, "cuda")
+    one_per_call = {"events_per_s": replica_throughput(one_call_s, n_one, world), "events": n_one,
+                    "inflight_calls": args.inflight, "path": "tpc_track_event, one event per call"}
 
     # ---- timed region 2 (per-event latency and the per-kernel roofline): one event at a time on
     # one stream, L2 flushed (untimed) before each step
@@ -335,7 +396,24 @@ def run_ours(args):
     step_ms = [s.elapsed_time(e) for s, e in zip(starts, ends)]
     serial = {"events_per_s": n_serial / (sum(step_ms) / 1e3), "ms_per_event": float(np.mean(step_ms)), "steps": n_serial,
               "ms_per_event_p50": float(np.median(step_ms)), "l2": "flushed before every event (512 MB write, untimed)"}
-    stats = {k: int(np.mean([s[k] for s in stats_all])) for k in ("row_visits", "candidates", "tracklets")}
+    # the step's own call (B events) one at a time, L2 flushed before each: the constructor's
+    # roofline is taken on it
+    n_bs = min(args.steps, 12)
+    b_stats, b_ms = [], []
+    barrier()
+    with torch.cuda.stream(stream):
+        for k in range(n_bs):
+            flush.fill_(float(k))
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            r = call(tr, calls[k % len(calls)], stream)
+            b.record(stream)
+            r.sync()
+            b_stats.append(r.stats())
+            r.release()
+            b_ms.append(a.elapsed_time(b))
+    b_stage = np.mean([np.array(s_["ms"]) for s_ in b_stats], axis=0)
+    stats = {k: int(np.mean([s_[k] for s_ in b_stats])) for k in ("row_visits", "candidates", "tracklets")}
     for t in trackers:
         t.set_timing(False)
 
@@ -468,25 +546,25 @@ def run_ours(args):
                 i = k % nf
                 if pend[i] is not None:
                     retire(i, count)
-                p = pool[k % len(pool)]
-                pend[i] = trackers[i].track_host(p[0], p[1], p[2], p[3], stream=streams[i])
+                c_ = calls[k % len(calls)]
+                pend[i] = trackers[i].track_batch_host(c_["hy"], c_["hz"], c_["hr"], c_["counts"], B, stream=streams[i])
                 if count:
-                    moved["h2d"] += p[4] * 9
+                    moved["h2d"] += c_["n"] * 9
             for i in range(nf):
                 if pend[i] is not None:
                     retire(i, count)
 
         pipelined(args.warmup * nf, False)
-        n_e2e = min(args.steps, 200)
+        n_e2e = min(args.steps, max(40, 600 // B))
         barrier()
         t0 = time.perf_counter()
         pipelined(n_e2e, True)
         wall_e2e = time.perf_counter() - t0
-        e2e_v = replica_throughput(reduce_max(wall_e2e, world, "cuda"), n_e2e, world)
+        e2e_v = replica_throughput(reduce_max(wall_e2e, world, "cuda"), n_e2e * B, world)
         e2e = {"value": e2e_v, "unit": "events/s", "h2d_bytes_per_step": int(moved["h2d"] / n_e2e),
-               "d2h_bytes_per_step": int(moved["d2h"] / n_e2e), "steps": n_e2e,
-               "path": "tpc_track_event_host (pinned host input) + tpc_result_copy_to_host, wall clock, "
-                       "%d events in flight on %d trackers" % (nf, nf),
+               "d2h_bytes_per_step": int(moved["d2h"] / n_e2e), "steps": n_e2e, "events_per_step": B,
+               "path": "tpc_track_batch_host (pinned host input, %d events per call) + tpc_result_copy_to_host, "
+                       "wall clock, %d calls in flight on %d trackers" % (B, nf, nf),
                "one_event_at_a_time": serial_e2e}
 
     if rank != 0:
@@ -496,13 +574,16 @@ def run_ours(args):
     stages = {n: round(float(v), 4) for n, v in zip(names, mean_stage)}
     peak, peak_kind = measured_peaks()
     cb = construct_bytes(stats)
-    con_ms = mean_stage[4]
+    con_ms = b_stage[4]
     achieved = cb / (con_ms * 1e-3) / 1e9
     traffic, winst, tnote = traffic_for_current_kernel()
-    roof = {"kernel": "k_construct (A5 tracklet construction)", "bound": "hbm", "achieved": achieved,
+    roof = {"kernel": "k_construct (A5 tracklet construction; %s)" % (
+                "pre-seeded, flat row search" if B * n_mean / 20 > 4 * 152 * 6 * 128 else "seeds walked per lane"),
+            "bound": "hbm", "achieved": achieved,
             "peak": peak, "unit": "GB/s", "frac": achieved / peak, "peak_source": peak_kind + " (hbm_gbs)",
             "traffic": traffic, "algorithmic_bytes": cb, "launch_ms": con_ms,
-            "timed_in": "timed region 2 (one event at a time)", "units": stats}
+            "timed_in": "the step's call (%d events) one at a time, L2 flushed before each; construction stage "
+                        "(work order, seeds and the constructor)" % B, "units": stats}
     if tnote:
         roof["traffic_note"] = tnote
     if winst:
@@ -517,12 +598,16 @@ def run_ours(args):
             "warmup": args.warmup, "ms_per_step": 1e3 * total_s / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": {"workload": WORKLOAD, "resident_events": args.resident,
-                       "clusters_per_event": int(round(n_mean)), "inflight_events": args.inflight,
+                       "clusters_per_event": int(round(n_mean)), "events_per_call": B,
+                       "inflight_calls": args.inflight,
                        "l2": "inputs larger than L2 (%d resident events, %.0f MB); no flush" % (
                            args.resident, args.resident * n_mean * 9 / 1e6),
                        "parallelism": "replicas" if world > 1 else "single GPU"},
             "clusters_per_s": value * n_mean, "tracks_per_event": int(np.mean(tracks)),
-            "one_event_at_a_time": serial, "stages_ms": stages, "global_tracking": global_line,
+            "one_event_per_call": one_per_call, "one_event_at_a_time": serial, "stages_ms": stages,
+            "one_call_at_a_time": {"ms_per_call": float(np.mean(b_ms)), "events_per_call": B,
+                                   "stages_ms": {n: round(float(v), 4) for n, v in zip(names, b_stage)},
+                                   "l2": "flushed before every call (512 MB write, untimed)"}, "global_tracking": global_line,
             "global_tracking_and_merger": merge_line,
             "gpu_launches": launches, "e2e": e2e, "roofline": roof, "clocks": clk,
             "wall_s_timed_region": wall}

@@ -210,6 +210,12 @@ int tpc_track_batch(tpc_tracker *tr, const float *y, const float *z, const uint8
 int tpc_track_event_host(tpc_tracker *tr, const float *y, const float *z, const uint8_t *row,
                          const int32_t *counts, int64_t n, void *stream, tpc_result **out);
 
+/* Same as tpc_track_batch, but y, z, row are HOST arrays (n_total clusters of
+ * n_events events, concatenated), copied to the device on `stream` first. */
+int tpc_track_batch_host(tpc_tracker *tr, const float *y, const float *z, const uint8_t *row,
+                         const int32_t *counts, int n_events, int64_t n_total, void *stream,
+                         tpc_result **out);
+
 /* Wait for the result's work and return its track and hit counts (either pointer
  * may be NULL).  Returns the device-side status of the call: TPC_OK,
  * TPC_ERR_INVALID_ARG (a cluster's row byte disagrees with counts),

@@ -755,7 +755,15 @@ extern "C" int tpc_track_event(tpc_tracker *tr, const float *y, const float *z, 
 extern "C" int tpc_track_event_host(tpc_tracker *tr, const float *y, const float *z, const uint8_t *row,
                                     const int32_t *counts, int64_t n, void *stream, tpc_result **out)
 {
-    if (!tr || !out || !counts || n < 0) return TPC_ERR_INVALID_ARG;
+    return tpc_track_batch_host(tr, y, z, row, counts, 1, n, stream, out);
+}
+
+extern "C" int tpc_track_batch_host(tpc_tracker *tr, const float *y, const float *z, const uint8_t *row,
+                                    const int32_t *counts, int n_events, int64_t n, void *stream,
+                                    tpc_result **out)
+{
+    NvtxRange nvtx("tpc_track_batch_host");
+    if (!tr || !out || !counts || n < 0 || n_events < 1) return TPC_ERR_INVALID_ARG;
     if (n > 0 && (!y || !z || !row)) return TPC_ERR_INVALID_ARG;
     *out = nullptr;
     std::lock_guard<std::mutex> g(tr->mu);
@@ -783,7 +791,7 @@ extern "C" int tpc_track_event_host(tpc_tracker *tr, const float *y, const float
         TPC_CUDA(cudaMemcpyAsync(dz, z, n * sizeof(float), cudaMemcpyHostToDevice, st));
         TPC_CUDA(cudaMemcpyAsync(dr, row, n, cudaMemcpyHostToDevice, st));
     }
-    return run(tr, dy, dz, dr, counts, 1, n, st, out);
+    return run(tr, dy, dz, dr, counts, n_events, n, st, out);
 }
 
 extern "C" int tpc_result_sync_counts(tpc_result *r, int64_t *n_tracks, int64_t *n_hits)

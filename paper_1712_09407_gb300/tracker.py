@@ -91,6 +91,8 @@ EXPORTS = {
                                 P(c_void_p)]),
     "tpc_track_event_host": (c_int, [c_void_p, c_void_p, c_void_p, c_void_p, c_void_p, c_int64, c_void_p,
                                      P(c_void_p)]),
+    "tpc_track_batch_host": (c_int, [c_void_p, c_void_p, c_void_p, c_void_p, c_void_p, c_int, c_int64, c_void_p,
+                                     P(c_void_p)]),
     "tpc_result_sync_counts": (c_int, [c_void_p, P(c_int64), P(c_int64)]),
     "tpc_result_get": (c_int, [c_void_p, P(tpc_track_view)]),
     "tpc_result_ready": (c_int, [c_void_p]),
@@ -222,6 +224,14 @@ def tpc_track_event_host(tr, y, z, row, counts, stream=None):
     n = int(y.shape[0])
     _check(lib().tpc_track_event_host(tr, _ptr(y), _ptr(z), _ptr(row), counts.ctypes.data, n, _stream(stream),
                                       ctypes.byref(h)), "tpc_track_event_host")
+    return h
+
+
+def tpc_track_batch_host(tr, y, z, row, counts, n_events, stream=None):
+    counts = np.ascontiguousarray(counts, dtype=np.int32)
+    h = c_void_p()
+    _check(lib().tpc_track_batch_host(tr, _ptr(y), _ptr(z), _ptr(row), counts.ctypes.data, int(n_events),
+                                      int(y.shape[0]), _stream(stream), ctypes.byref(h)), "tpc_track_batch_host")
     return h
 
 
@@ -490,6 +500,9 @@ class Tracker:
 
     def track_host(self, y, z, row, counts, stream=None) -> Result:
         return Result(tpc_track_event_host(self.handle, y, z, row, counts, stream), self)
+
+    def track_batch_host(self, y, z, row, counts, n_events, stream=None) -> Result:
+        return Result(tpc_track_batch_host(self.handle, y, z, row, counts, n_events, stream), self)
 
     def set_timing(self, enable=True):
         tpc_tracker_set_timing(self.handle, enable)

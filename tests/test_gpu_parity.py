@@ -290,6 +290,15 @@ def test_batch_equals_one_at_a_time():
         hb = np.concatenate([b["hits"][f:f + n] for f, n in zip(b["first"][sel], b["nhits"][sel])])
         assert np.array_equal(hb - off, s["hits"])
         off += ev.n
+    # the same batch from host arrays
+    hy, hz, hr = (np.concatenate([getattr(e, f) for e in evs]) for f in ("y", "z", "row"))
+    res = tr.track_batch_host(torch.from_numpy(hy).pin_memory(), torch.from_numpy(hz).pin_memory(),
+                              torch.from_numpy(hr).pin_memory(), counts, len(evs))
+    res.sync()
+    h = res.to_numpy()
+    res.release()
+    for k in b:
+        assert np.array_equal(b[k], h[k]), k
     tr.close()
 
 
