@@ -128,13 +128,82 @@ __global__ void __launch_bounds__(256) k_seed(const DevConst c, const Workspace 
     }
 }
 
+// Row search and Kalman update of one lane's row visit: the best cluster within the chi2 gate
+// updates the state (and, on the inward pass, is recorded as a hit), otherwise the row is a miss.
+// Returns true when the pass stops (max_miss misses in a row).
+template <bool FLAT>
+__device__ __forceinline__ bool search_and_update(const DevConst &c, const Workspace &w, int4 rg, float4 gr, float xr,
+                                                  KF &pr, KF &st, float &xs, int phase, int t, int r, int &rlast,
+                                                  int &miss, int &n, float &chi2sum, int &visits, int &cands)
+{
+    visits++;
+    const Gain g = residual_cov_inv(pr, c);
+    float chi2 = 0.0f;
+    float2 q_unused;      // reloaded below instead: keeping it live costs spills at 80 registers
+    const int bl = search_cells<FLAT>(c, w.yz + rg.x, w.orig + rg.x, w.cell + rg.y, gr, rg.z, rg.w, pr, g, chi2,
+                                      q_unused, cands);
+    const int b = bl < 0 ? -1 : rg.x + bl;
+    if (b >= 0 && chi2 <= c.chi2max) {
+        const float2 q = __ldg(w.yz + b);
+        if (phase == 2) {
+            chi2sum = chi2sum + chi2;
+            if (TPC_IDX(n, c.nr, w.err, c, 4)) w.tl_hits[(int64_t)t * c.nr + n] = b;
+            n++;
+        } else {
+            rlast = r;
+        }
+        kf_update(pr, g, q.x, q.y);
+        st = pr;
+        xs = xr;
+        miss = 0;
+        return false;
+    }
+    return ++miss >= c.max_miss;
+}
+
+// After a row visit: the next row of the pass, or the pass's end.  The outward pass turns into
+// the inward pass from its last cluster with a fresh covariance (no cluster: no tracklet); the
+// inward pass writes the tracklet, its state at the innermost fitted cluster.
+template <bool GLOBAL>
+__device__ __forceinline__ void next_row(const DevConst &c, const Workspace &w, bool stop, int &phase, int t, int &r,
+                                         int rlast, int &miss, int &n, float &chi2sum, KF &st, float xs, int orig0)
+{
+    if (!stop) {
+        r += (phase == 1) ? 1 : -1;
+        if (r < 0 || r >= c.nr) stop = true;
+    }
+    if (stop) {
+        if (phase == 1) {
+            if (rlast < 0) {
+                phase = 0;
+            } else {
+                if (GLOBAL) write_outer(w, t, st, xs);   // outer end for global tracking
+                set_seed_cov(st, c);
+                r = rlast;
+                miss = 0;
+                n = 0;
+                chi2sum = 0.0f;
+                phase = 2;
+            }
+        } else {
+            write_tracklet(c, w, t, st, xs, n, chi2sum, orig0);
+            phase = 0;
+        }
+    }
+}
+
 // 128 threads and 6 resident CTAs per SM: 80 registers without spills (measured fastest).
 // GLOBAL: also store the outward pass's final state (the outer end for global tracking); a
 // separate instance so that the plain tracker keeps its register allocation.
-// PRESEED: seeds come from k_seed's records and the row search runs as one flat loop (many
-// tracklets per lane: throughput-bound); otherwise each lane walks its tracklet's chain when it
-// takes the tracklet and the row search runs as nested loops (few tracklets per lane, where the
-// latency of the last long tracklets decides the time).
+// PRESEED selects between two shapes of the same loop (same rows, same arithmetic, same results):
+// - false (few tracklets per lane, one event per call): a lane walks its tracklet's chain for the
+//   seed when it takes the tracklet, leaves the loop on its own when the queue is empty, and the
+//   row search runs as nested loops.  The time is set by the last long tracklets, so no lane
+//   waits for another.
+// - true (several tracklets per lane): the seed is read from k_seed's record; the warp meets
+//   once per row visit after the transport, so that lanes that took a tracklet or skipped the
+//   transport search together instead of in separate passes of the visit, and the row search
+//   runs as one flat loop.  Throughput-bound, so fewer issued instructions win over waiting.
 template <bool GLOBAL, bool PRESEED>
 __global__ void __launch_bounds__(128, 6)
 k_construct(const DevConst c, const Workspace w)
@@ -145,104 +214,98 @@ k_construct(const DevConst c, const Workspace w)
     float xs = 0.0f, chi2sum = 0.0f;
     KF st;
     int visits = 0, cands = 0;
-    while (true) {
-        if (phase == 0) {
-            const int q = atomicAdd(&w.counters[CNT_QUEUE], 1);
-            if (q >= T) break;
-            int r0;
-            if (PRESEED) {
-                const float4 sa = w.seeds[2 * q], sb = w.seeds[2 * q + 1];
-                t = __float_as_int(sb.y);
-                if (t < 0) continue;                     // unusable seed: the tracklet stays empty
-                const int packed = __float_as_int(sb.z);
-                sec = packed >> 16;
-                r0 = packed & 0xff;
-                orig0 = __float_as_int(sb.w);
-                st.p0 = sa.x;
-                st.p1 = sa.y;
-                st.p2 = sa.z;
-                st.p3 = sa.w;
-                st.p4 = sb.x;
-                set_seed_cov(st, c);
-            } else {
+    if (!PRESEED) {
+        while (true) {
+            if (phase == 0) {
+                const int q = atomicAdd(&w.counters[CNT_QUEUE], 1);
+                if (q >= T) break;
                 t = w.order[q];
                 const int4 sd = w.starts[t];
                 sec = sd.w >> 16;
-                r0 = sd.w & 0xff;
+                const int r0 = sd.w & 0xff;
                 orig0 = w.orig[sd.x];
                 w.tl_n[t] = 0;
                 w.tl_key[t] = 0ull;
                 if (!seed_tracklet(c, w, sd, st)) continue;
-            }
-            phase = 1;
-            r = r0;
-            xs = c.row_x[r0];
-            rlast = -1;
-            miss = 0;
-        }
-        // one row visit; the row's search record is loaded first so that its latency overlaps
-        // the transport arithmetic
-        const int unit = sec * c.nr + r;
-        const int4 rg = __ldg(&w.rgi[unit]);
-        const float4 gr = __ldg(&w.grid[unit]);
-        const float xr = c.row_x[r];
-        KF pr = st;
-        bool stop = false;
-        if (xr != xs && !propagate(pr, xr - xs, c)) {
-            stop = true;
-        } else if (fabsf(pr.p0) > __fmaf_rn(xr, c.th, c.margin)) {
-            stop = true;
-        } else {
-            visits++;
-            const Gain g = residual_cov_inv(pr, c);
-            float chi2 = 0.0f;
-            float2 q_unused;      // reloaded below instead: keeping it live costs spills at 80 registers
-            const int bl = search_cells<PRESEED>(c, w.yz + rg.x, w.orig + rg.x, w.cell + rg.y, gr, rg.z, rg.w, pr, g, chi2,
-                                        q_unused, cands);
-            const int b = bl < 0 ? -1 : rg.x + bl;
-            if (b >= 0 && chi2 <= c.chi2max) {
-                const float2 q = __ldg(w.yz + b);
-                if (phase == 2) {
-                    chi2sum = chi2sum + chi2;
-                    if (TPC_IDX(n, c.nr, w.err, c, 4)) w.tl_hits[(int64_t)t * c.nr + n] = b;
-                    n++;
-                } else {
-                    rlast = r;
-                }
-                kf_update(pr, g, q.x, q.y);
-                st = pr;
-                xs = xr;
+                phase = 1;
+                r = r0;
+                xs = c.row_x[r0];
+                rlast = -1;
                 miss = 0;
-            } else if (++miss >= c.max_miss) {
+            }
+            // one row visit; the row's search record is loaded first so that its latency overlaps
+            // the transport arithmetic
+            const int unit = sec * c.nr + r;
+            const int4 rg = __ldg(&w.rgi[unit]);
+            const float4 gr = __ldg(&w.grid[unit]);
+            const float xr = c.row_x[r];
+            KF pr = st;
+            bool stop = false;
+            if (xr != xs && !propagate(pr, xr - xs, c)) {
                 stop = true;
-            }
-        }
-        if (!stop) {
-            r += (phase == 1) ? 1 : -1;
-            if (r < 0 || r >= c.nr) stop = true;
-        }
-        if (stop) {
-            if (phase == 1) {
-                if (rlast < 0) {
-                    phase = 0;
-                } else {
-                    if (GLOBAL) write_outer(w, t, st, xs);   // outer end for global tracking
-                    set_seed_cov(st, c);
-                    r = rlast;
-                    miss = 0;
-                    n = 0;
-                    chi2sum = 0.0f;
-                    phase = 2;
-                }
+            } else if (fabsf(pr.p0) > __fmaf_rn(xr, c.th, c.margin)) {
+                stop = true;
             } else {
-                // the state sits at the innermost fitted cluster
-                write_tracklet(c, w, t, st, xs, n, chi2sum, orig0);
-                phase = 0;
+                stop = search_and_update<false>(c, w, rg, gr, xr, pr, st, xs, phase, t, r, rlast, miss, n, chi2sum,
+                                                visits, cands);
             }
+            next_row<GLOBAL>(c, w, stop, phase, t, r, rlast, miss, n, chi2sum, st, xs, orig0);
+        }
+        __syncwarp();
+    } else {
+        bool drained = false;     // this lane found the queue empty; the warp leaves when all have
+        while (true) {
+            if (phase == 0 && !drained) {
+                const int q = atomicAdd(&w.counters[CNT_QUEUE], 1);
+                if (q >= T) {
+                    drained = true;
+                } else {
+                    const float4 sa = w.seeds[2 * q], sb = w.seeds[2 * q + 1];
+                    t = __float_as_int(sb.y);
+                    if (t >= 0) {                            // t < 0: unusable seed, the tracklet stays empty
+                        const int packed = __float_as_int(sb.z);
+                        sec = packed >> 16;
+                        r = packed & 0xff;
+                        orig0 = __float_as_int(sb.w);
+                        st.p0 = sa.x;
+                        st.p1 = sa.y;
+                        st.p2 = sa.z;
+                        st.p3 = sa.w;
+                        st.p4 = sb.x;
+                        set_seed_cov(st, c);
+                        xs = c.row_x[r];
+                        rlast = -1;
+                        miss = 0;
+                        phase = 1;
+                    }
+                }
+            }
+            if (__all_sync(kFull, phase == 0 && drained)) break;
+            // transport to the row (lanes with a tracklet only), then the searching lanes meet
+            KF pr = st;
+            int4 rg = make_int4(0, 0, 0, 0);
+            float4 gr = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+            float xr = 0.0f;
+            bool stop = phase == 0;
+            if (!stop) {
+                const int unit = sec * c.nr + r;
+                rg = __ldg(&w.rgi[unit]);
+                gr = __ldg(&w.grid[unit]);
+                xr = c.row_x[r];
+                if (xr != xs && !propagate(pr, xr - xs, c)) stop = true;
+                else if (fabsf(pr.p0) > __fmaf_rn(xr, c.th, c.margin)) stop = true;
+            }
+            const unsigned searching = __ballot_sync(kFull, !stop);
+            if (phase == 0) continue;
+            if (!stop) {
+                __syncwarp(searching);
+                stop = search_and_update<true>(c, w, rg, gr, xr, pr, st, xs, phase, t, r, rlast, miss, n, chi2sum,
+                                               visits, cands);
+            }
+            next_row<GLOBAL>(c, w, stop, phase, t, r, rlast, miss, n, chi2sum, st, xs, orig0);
         }
     }
     // visit statistics, one atomic per warp
-    __syncwarp();
     for (int o = 16; o > 0; o >>= 1) {
         visits += __shfl_xor_sync(kFull, visits, o);
         cands += __shfl_xor_sync(kFull, cands, o);
