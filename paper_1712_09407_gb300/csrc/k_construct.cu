@@ -131,7 +131,6 @@ __global__ void __launch_bounds__(256) k_seed(const DevConst c, const Workspace 
 // Row search and Kalman update of one lane's row visit: the best cluster within the chi2 gate
 // updates the state (and, on the inward pass, is recorded as a hit), otherwise the row is a miss.
 // Returns true when the pass stops (max_miss misses in a row).
-template <bool FLAT>
 __device__ __forceinline__ bool search_and_update(const DevConst &c, const Workspace &w, int4 rg, float4 gr, float xr,
                                                   KF &pr, KF &st, float &xs, int phase, int t, int r, int &rlast,
                                                   int &miss, int &n, float &chi2sum, int &visits, int &cands)
@@ -140,8 +139,8 @@ __device__ __forceinline__ bool search_and_update(const DevConst &c, const Works
     const Gain g = residual_cov_inv(pr, c);
     float chi2 = 0.0f;
     float2 q_unused;      // reloaded below instead: keeping it live costs spills at 80 registers
-    const int bl = search_cells<FLAT>(c, w.yz + rg.x, w.orig + rg.x, w.cell + rg.y, gr, rg.z, rg.w, pr, g, chi2,
-                                      q_unused, cands);
+    const int bl = search_cells(c, w.yz + rg.x, w.orig + rg.x, w.cell + rg.y, gr, rg.z, rg.w, pr, g, chi2, q_unused,
+                                cands);
     const int b = bl < 0 ? -1 : rg.x + bl;
     if (b >= 0 && chi2 <= c.chi2max) {
         const float2 q = __ldg(w.yz + b);
@@ -197,13 +196,12 @@ __device__ __forceinline__ void next_row(const DevConst &c, const Workspace &w, 
 // separate instance so that the plain tracker keeps its register allocation.
 // PRESEED selects between two shapes of the same loop (same rows, same arithmetic, same results):
 // - false (few tracklets per lane, one event per call): a lane walks its tracklet's chain for the
-//   seed when it takes the tracklet, leaves the loop on its own when the queue is empty, and the
-//   row search runs as nested loops.  The time is set by the last long tracklets, so no lane
-//   waits for another.
+//   seed when it takes the tracklet and leaves the loop on its own when the queue is empty.  The
+//   time is set by the last long tracklets, so no lane waits for another.
 // - true (several tracklets per lane): the seed is read from k_seed's record; the warp meets
 //   once per row visit after the transport, so that lanes that took a tracklet or skipped the
-//   transport search together instead of in separate passes of the visit, and the row search
-//   runs as one flat loop.  Throughput-bound, so fewer issued instructions win over waiting.
+//   transport search together instead of in separate passes of the visit.  Throughput-bound, so
+//   fewer issued instructions win over waiting.
 template <bool GLOBAL, bool PRESEED>
 __global__ void __launch_bounds__(128, 6)
 k_construct(const DevConst c, const Workspace w)
@@ -246,7 +244,7 @@ k_construct(const DevConst c, const Workspace w)
             } else if (fabsf(pr.p0) > __fmaf_rn(xr, c.th, c.margin)) {
                 stop = true;
             } else {
-                stop = search_and_update<false>(c, w, rg, gr, xr, pr, st, xs, phase, t, r, rlast, miss, n, chi2sum,
+                stop = search_and_update(c, w, rg, gr, xr, pr, st, xs, phase, t, r, rlast, miss, n, chi2sum,
                                                 visits, cands);
             }
             next_row<GLOBAL>(c, w, stop, phase, t, r, rlast, miss, n, chi2sum, st, xs, orig0);
@@ -299,7 +297,7 @@ k_construct(const DevConst c, const Workspace w)
             if (phase == 0) continue;
             if (!stop) {
                 __syncwarp(searching);
-                stop = search_and_update<true>(c, w, rg, gr, xr, pr, st, xs, phase, t, r, rlast, miss, n, chi2sum,
+                stop = search_and_update(c, w, rg, gr, xr, pr, st, xs, phase, t, r, rlast, miss, n, chi2sum,
                                                visits, cands);
             }
             next_row<GLOBAL>(c, w, stop, phase, t, r, rlast, miss, n, chi2sum, st, xs, orig0);

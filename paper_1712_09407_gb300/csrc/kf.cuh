@@ -242,13 +242,11 @@ struct BestCand {
 // within the row, or -1; the best cluster's (y, z) in best_yz.  used (optional): clusters with a
 // nonzero byte are skipped.
 //
-// FLAT selects the loop shape; both visit the same candidates in the same order (cell rows iz
-// ascending, slots ascending), so the result is the same.  Nested loops (a loop per cell row)
-// keep one lane's search short, which matters when few warps are left to hide latency.  The flat
-// loop (an iteration either moves to the next cell row or tests one candidate) lets a warp run as
-// many iterations as its busiest lane has candidates plus cell rows instead of the sum over cell
-// rows of the busiest lane in each, which matters when the constructor is throughput-bound.
-template <bool FLAT = false>
+// Candidates are visited cell row by cell row (iz ascending, slots ascending) in one flat loop:
+// an iteration tests one candidate and moves on to the next non-empty cell row within the same
+// iteration, so a warp runs as many iterations as its busiest lane has candidates, instead of
+// the sum over cell rows of the busiest lane in each (nested loops) or one more iteration per
+// cell row (a loop whose iterations either move or test).
 __device__ __forceinline__ int search_cells(const DevConst &c, const float2 *yz, const int32_t *orig,
                                             const int32_t *cell, const float4 gr, int ny, int nz, const KF &pr,
                                             const Gain &g, float &chi2_out, float2 &best_yz, int &ncand,
@@ -261,57 +259,30 @@ __device__ __forceinline__ int search_cells(const DevConst &c, const float2 *yz,
     const int iy1 = cell1(y + wy + kBinSlack, gr.x, gr.z, ny);
     const int iz0 = cell1(z - wz - kBinSlack, gr.y, gr.w, nz);
     const int iz1 = cell1(z + wz + kBinSlack, gr.y, gr.w, nz);
-    if (FLAT) {
-        BestCand b;
-        int iz = iz0 - 1, j = 0, e = 0;
-        while (true) {
-            if (j >= e) {
-                if (++iz > iz1) break;
-                j = cell[iz * ny + iy0];
-                e = cell[iz * ny + iy1 + 1];
-                ncand += e - j;
-                continue;
-            }
-            const int k = j++;
-            const float2 q = yz[k];                     // issued together with the used[] load
-            if (used && used[k]) continue;
-            if (!(fabsf(q.x - y) <= wy && fabsf(q.y - z) <= wz)) continue;
-            b.offer(k, q, chi2_of(g, q.x - y, q.y - z), orig);
-        }
-        chi2_out = b.bc;
-        best_yz = b.bq;
-        return b.best;
+    BestCand b;
+    int iz = iz0 - 1, j = 0, e = 0;
+    while (j >= e && iz < iz1) {                    // first non-empty cell row
+        ++iz;
+        j = cell[iz * ny + iy0];
+        e = cell[iz * ny + iy1 + 1];
+        ncand += e - j;
     }
-    int best = -1, borig = -1;       // borig: input index of the best slot, loaded on the first tie
-    float bc = 0.0f;
-    float2 bq = make_float2(0.0f, 0.0f);
-    for (int iz = iz0; iz <= iz1; iz++) {
-        const int a = cell[iz * ny + iy0], e = cell[iz * ny + iy1 + 1];
-        ncand += e - a;
-        for (int j = a; j < e; j++) {
-            const float2 q = yz[j];                     // issued together with the used[] load
-            if (used && used[j]) continue;
-            if (!(fabsf(q.x - y) <= wy && fabsf(q.y - z) <= wz)) continue;
-            const float x2 = chi2_of(g, q.x - y, q.y - z);
-            if (best < 0 || x2 < bc) {                  // the same rule as BestCand::offer
-                best = j;
-                bc = x2;
-                bq = q;
-                borig = -1;
-            } else if (x2 == bc) {
-                if (borig < 0) borig = orig[best];
-                const int o = orig[j];
-                if (o < borig) {
-                    best = j;
-                    bq = q;
-                    borig = o;
-                }
-            }
+    while (j < e) {
+        const int k = j++;
+        const float2 q = yz[k];                     // issued together with the used[] load
+        while (j >= e && iz < iz1) {                // next non-empty cell row, in the same iteration
+            ++iz;
+            j = cell[iz * ny + iy0];
+            e = cell[iz * ny + iy1 + 1];
+            ncand += e - j;
         }
+        if (used && used[k]) continue;
+        if (!(fabsf(q.x - y) <= wy && fabsf(q.y - z) <= wz)) continue;
+        b.offer(k, q, chi2_of(g, q.x - y, q.y - z), orig);
     }
-    chi2_out = bc;
-    best_yz = bq;
-    return best;
+    chi2_out = b.bc;
+    best_yz = b.bq;
+    return b.best;
 }
 
 // Writes a finished tracklet: state at its innermost fitted cluster, chi2, weight and the 64-bit
