@@ -235,7 +235,10 @@ constexpr int kDList = 12;   // row k-1 candidates kept per cluster before falli
 
 // Best (u, d) pair for cluster (yc, zc): the row k-1 candidates inside the window are listed once,
 // then every row k+1 candidate inside its window is paired with each of them.  More than kDList
-// row k-1 candidates (very dense rows) use search_pairs_full, which gives the same answer.
+// row k-1 candidates (very dense rows) use search_pairs_full, which gives the same answer.  Both
+// rows' candidates are visited cell row by cell row, slots ascending, in flat loops that move on
+// to the next non-empty cell row within a candidate's iteration (a warp runs as many iterations as
+// its busiest lane has candidates).
 __device__ __forceinline__ void search_pairs(const DevConst &c, const RowView &U, const RowView &D, float yc,
                                              float zc, float wyu, float wzu, float wyd, float wzd, float w,
                                              float gate, int &out_u, int &out_d)
@@ -248,15 +251,26 @@ __device__ __forceinline__ void search_pairs(const DevConst &c, const RowView &U
     int dlj[kDList];
     int nd = 0;
     bool over = false;
-    for (int izd = iz0d; izd <= iz1d; izd++) {
-        const int ad = D.cell[izd * D.ny + iy0d], ed = D.cell[izd * D.ny + iy1d + 1];
-        for (int jd = ad; jd < ed; jd++) {
-            const float2 pd = D.yz[jd];
+    {
+        int izd = iz0d - 1, jd = 0, ed = 0;
+        while (jd >= ed && izd < iz1d) {
+            ++izd;
+            jd = D.cell[izd * D.ny + iy0d];
+            ed = D.cell[izd * D.ny + iy1d + 1];
+        }
+        while (jd < ed) {
+            const int k = jd++;
+            const float2 pd = D.yz[k];
+            while (jd >= ed && izd < iz1d) {
+                ++izd;
+                jd = D.cell[izd * D.ny + iy0d];
+                ed = D.cell[izd * D.ny + iy1d + 1];
+            }
             if (!(fabsf(pd.x - yc) <= wyd && fabsf(pd.y - zc) <= wzd)) continue;
             if (nd < kDList) {
                 dly[nd] = pd.x;
                 dlz[nd] = pd.y;
-                dlj[nd] = jd;
+                dlj[nd] = k;
                 nd++;
             } else {
                 over = true;
@@ -276,10 +290,21 @@ __device__ __forceinline__ void search_pairs(const DevConst &c, const RowView &U
     const int iz1u = cell1(zc + wzu + kBinSlack, U.zmin, U.idz, U.nz);
     int bu = -1, bd = -1, bou = 0, bod = 0;
     float best = 0.0f;
-    for (int izu = iz0u; izu <= iz1u; izu++) {
-        const int au = U.cell[izu * U.ny + iy0u], eu = U.cell[izu * U.ny + iy1u + 1];
-        for (int ju = au; ju < eu; ju++) {
+    int izu = iz0u - 1, jn = 0, eu = 0;
+    while (jn >= eu && izu < iz1u) {
+        ++izu;
+        jn = U.cell[izu * U.ny + iy0u];
+        eu = U.cell[izu * U.ny + iy1u + 1];
+    }
+    while (jn < eu) {
+        const int ju = jn++;
+        {   // one row k+1 candidate
             const float2 pu = U.yz[ju];
+            while (jn >= eu && izu < iz1u) {
+                ++izu;
+                jn = U.cell[izu * U.ny + iy0u];
+                eu = U.cell[izu * U.ny + iy1u + 1];
+            }
             if (!(fabsf(pu.x - yc) <= wyu && fabsf(pu.y - zc) <= wzu)) continue;
             const int ou = U.orig[ju];
             for (int k = 0; k < nd; k++) {
