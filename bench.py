@@ -579,7 +579,7 @@ def run_ours(args):
     achieved = cb / (con_ms * 1e-3) / 1e9
     traffic, winst, tnote = traffic_for_current_kernel()
     roof = {"kernel": "k_construct (A5 tracklet construction; %s)" % (
-                "pre-seeded, lanes meeting per row" if B * n_mean / 20 > 4 * 152 * 6 * 128 else "seeds walked per lane"),
+                "pre-seeded, lanes meeting per row" if B * n_mean / 20 > 2 * 152 * 6 * 128 else "seeds walked per lane"),
             "bound": "hbm", "achieved": achieved,
             "peak": peak, "unit": "GB/s", "frac": achieved / peak, "peak_source": peak_kind + " (hbm_gbs)",
             "traffic": traffic, "algorithmic_bytes": cb, "launch_ms": con_ms,

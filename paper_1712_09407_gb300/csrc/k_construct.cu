@@ -323,10 +323,11 @@ int launch_construct(const DevConst &c, const Workspace &w, const LaunchCfg &lc,
                                                       lc.construct_block, 0);
         per_sm = occ > 0 ? occ : 1;
     }
-    // seed kernel when the call is expected to give each resident lane several tracklets (about one
-    // start hit per 20 clusters in central-like events; 6 resident CTAs per SM)
+    // seed kernel (and the pre-seeded constructor) when the call is expected to give each resident
+    // lane at least two tracklets (about one start hit per 20 clusters in central-like events; 6
+    // resident CTAs per SM): two central-like events per call and more
     const int64_t lanes = (int64_t)lc.num_sms * 6 * lc.construct_block;
-    const bool preseed = lc.seed_kernel > 0 || (lc.seed_kernel < 0 && lc.n_clusters / 20 > 4 * lanes);
+    const bool preseed = lc.seed_kernel > 0 || (lc.seed_kernel < 0 && lc.n_clusters / 20 > 2 * lanes);
     // groups of order_group slots, as many as the histogram's kOrderCursors buckets hold
     const int kb = order_kb(c.nr), max_groups = kOrderCursors / kb;
     int64_t gs = lc.order_group > 0 ? lc.order_group : lc.n_slots + 1;
