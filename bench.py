@@ -162,10 +162,15 @@ def construct_bytes(stats):
 
 
 def construct_source_hash():
-    """Hash of the sources that make up k_construct (its file and the headers it inlines)."""
+    """Hash of the sources that make up k_construct (its file and the headers it inlines), with
+    comments and whitespace removed, so that only a change of the code invalidates the counters."""
+    import re
     h = hashlib.sha256()
     for f in CONSTRUCT_SRC:
-        h.update(open(f, "rb").read())
+        src = open(f).read()
+        src = re.sub(r"/\*.*?\*/", " ", src, flags=re.S)
+        src = re.sub(r"//[^\n]*", " ", src)
+        h.update(" ".join(src.split()).encode())
     return h.hexdigest()[:16]
 
 

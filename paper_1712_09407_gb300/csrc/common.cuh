@@ -13,9 +13,9 @@ constexpr int kCellMax = 1024;      // grid cells per row unit (host clamps)
 constexpr int kSlotAlign = 8;       // sorted row segments start on 8-element (32 B) boundaries
 constexpr int kCellAlign = 4;       // cell-start segments start on 16 B boundaries
 constexpr unsigned kFull = 0xffffffffu;
-constexpr int kOrderBuckets = 512;  // >= 2 * kMaxRows + 2 (expected-work keys)
-constexpr int kOrderCursors = 6144; // buckets of the constructor's grouped order (the scatter holds two
-                                    // arrays of them in 48 KB of shared memory); cursors follow them
+constexpr int kOrderCursors = 6144; // buckets of the constructor's grouped order, at least one group of
+                                    // 2 kMaxRows + 2 expected-work keys (the scatter holds two arrays
+                                    // of them in 48 KB of shared memory); cursors follow them
 
 // Error word layout in the workspace: [0] status, [1] event, [2] sector, [3] stage.
 enum { ERR_STATUS = 0, ERR_EVENT = 1, ERR_SECTOR = 2, ERR_STAGE = 3 };

@@ -20,15 +20,15 @@ namespace tpc {
 // clusters usually belongs to a real track, which runs outwards from its start row to the last
 // row and back to row 0: about 2 * n_rows - start row visits.  Shorter chains are mostly noise
 // triplets that stop after a few rows.  In a call with many events the tracklets are first
-// grouped by the slot of their start cluster (groups of gslots consecutive slots, a few
-// central-like events): the queue finishes one group's tracklets before the next group's, so
-// the rows the resident lanes search stay in L2.  The order only changes which lane builds
+// grouped by the slot of their start cluster (groups of gslots consecutive slots, about one
+// central-like event by default): the queue finishes one group's tracklets before the next
+// group's, so the rows the resident lanes search stay in L2.  The order only changes which lane builds
 // which tracklet when; every tracklet's result is the same.
 // ---------------------------------------------------------------------------------------------
 __device__ __forceinline__ int work_key(const DevConst &c, int packed)
 {
     const int len = (packed >> 8) & 0xff, r0 = packed & 0xff;
-    return len >= 4 ? 2 * c.nr - r0 + 1 : 0;       // 0 .. 2 nr + 1 < kOrderBuckets
+    return len >= 4 ? 2 * c.nr - r0 + 1 : 0;       // 0 .. 2 nr + 1 < order_kb(nr)
 }
 
 // Buckets per group: the work keys 0 .. 2 nr + 1, rounded up to a multiple of 32.
