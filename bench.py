@@ -189,7 +189,28 @@ def traffic_for_current_kernel():
 # ------------------------------------------------------------------------------------------------
 # CPU oracle legs
 # ------------------------------------------------------------------------------------------------
+def cpu_model() -> str:
+    """The host CPU's model name (lscpu, else /proc/cpuinfo, else the architecture)."""
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.startswith("Model name:"):
+                return line.split(":", 1)[1].strip()
+    except (OSError, subprocess.SubprocessError):
+        pass
+    try:
+        for line in open("/proc/cpuinfo"):
+            if line.lower().startswith("model name"):
+                return line.split(":", 1)[1].strip()
+    except OSError:
+        pass
+    import platform
+    return platform.machine()
+
+
 def oracle_timing(ev, min_seconds=10.0, max_runs=60, min_runs=1):
+    """The float-mode oracle on the host cores (OpenMP over the 36 sectors), then once on one
+    thread (a bounded sample: one event)."""
     import oracle
     cfg = oracle.config_for(ev.geometry)
     times = []
@@ -199,9 +220,14 @@ def oracle_timing(ev, min_seconds=10.0, max_runs=60, min_runs=1):
         oracle.track_event(cfg, ev.y, ev.z, ev.row, ev.counts, precision=32)
         times.append(time.perf_counter() - t0)
     cores = os.cpu_count()
+    t0 = time.perf_counter()
+    oracle.track_event(oracle.config_for(ev.geometry, n_threads=1), ev.y, ev.z, ev.row, ev.counts, precision=32)
+    t_one = time.perf_counter() - t0
     return dict(value=len(times) / sum(times), unit="events/s", cores=cores, kind="oracle",
                 sample="full central-like event (3.29 M clusters), float-mode C oracle, OpenMP over the 36 "
-                       "sectors on %d threads, %d runs, %.1f s" % (cores, len(times), sum(times)))
+                       "sectors on %d threads, %d runs, %.1f s" % (cores, len(times), sum(times)),
+                single_thread={"value": 1.0 / t_one, "unit": "events/s", "sample": "one event on one thread"},
+                cpu_model=cpu_model())
 
 
 def run_reference(args):
