@@ -112,6 +112,11 @@ def lib():
             L.orc_seed_f64.argtypes = [P, P, P, ctypes.c_double, ctypes.c_double, P]
             L.orc_asin_ratio_f32.restype = ctypes.c_float
             L.orc_asin_ratio_f32.argtypes = [ctypes.c_float]
+            for pre in ("f64", "f32"):
+                f = getattr(L, "orc_select_" + pre)
+                f.restype = None
+                f.argtypes = [ctypes.c_int64, P, P, P, ctypes.c_int, ctypes.c_double, ctypes.c_double,
+                              ctypes.c_int64, P, P]
             L.orc_bin_row_f32.argtypes = [P, P, ctypes.c_int, ctypes.c_float, ctypes.c_float,
                                           ctypes.c_float, ctypes.c_float, ctypes.c_int, ctypes.c_int,
                                           P, P, P]
@@ -310,6 +315,25 @@ def track_event(cfg: Config, y, z, row, counts, precision: int = 32) -> Result:
     finally:
         L.orc_result_free(h)
     return Result(info=d, **out)
+
+
+def select(tracklets, alpha, beta, n_clusters, n_rows=159, precision: int = 64, library=None):
+    """Section 3.1 on given tracklets, as the tracker applies it (orc_select): ``tracklets`` is a
+    list of (cluster indices, fit chi2).  Returns (weights, owner of every cluster, -1 for none).
+    ``library``: another build of the oracle (a ctypes library) instead of this one."""
+    L = library if library is not None else lib()
+    T = len(tracklets)
+    nhits = np.array([len(h) for h, _ in tracklets], dtype=np.int32)
+    chi2 = np.array([c for _, c in tracklets], dtype=np.float64)
+    hits = np.full((max(T, 1), n_rows), -1, dtype=np.int32)
+    for t, (h, _) in enumerate(tracklets):
+        hits[t, :len(h)] = h
+    w = np.zeros(max(T, 1), dtype=np.float64)
+    owner = np.zeros(max(n_clusters, 1), dtype=np.int32)
+    fn = L.orc_select_f64 if precision == 64 else L.orc_select_f32
+    fn(T, nhits.ctypes.data, chi2.ctypes.data, hits.ctypes.data, n_rows, float(alpha), float(beta), n_clusters,
+       w.ctypes.data, owner.ctypes.data)
+    return w[:T], owner[:n_clusters]
 
 
 def propagate(state, cov15, x0, x1, bz=0.5, sin_max=0.99, precision: int = 64):

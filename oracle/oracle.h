@@ -135,6 +135,15 @@ int orc_chi2_5_f64(const double *A15, const double *d5, double *chi2);
 int orc_seed_f64(const double *x3, const double *y3, const double *z3, double bz, double sin_max,
                  double *state);
 
+/* Cluster weights and ownership of Section 3.1 on given tracklets, exactly as the tracker
+ * applies them: w_out[t] = n (alpha - (chi2 / ndf) / beta) with ndf = 2 n - 5 (-inf when
+ * ndf < 1), owner_out[c] = the tracklet of largest weight holding cluster c, the lower index of
+ * equal weights, -1 if none.  hits: [T * n_rows], the first nhits[t] entries of row t used. */
+void orc_select_f64(int64_t T, const int32_t *nhits, const double *chi2, const int32_t *hits, int n_rows,
+                    double alpha, double beta, int64_t n_clusters, double *w_out, int32_t *owner_out);
+void orc_select_f32(int64_t T, const int32_t *nhits, const double *chi2, const int32_t *hits, int n_rows,
+                    double alpha, double beta, int64_t n_clusters, double *w_out, int32_t *owner_out);
+
 #ifdef __cplusplus
 }
 #endif

@@ -499,6 +499,35 @@ static int32_t search_row(Sector *S, const K *k, const real *Y, const real *Zc, 
     return best;
 }
 
+/* Section 3.1: the weight of a tracklet of n clusters whose fit collected chi2sum,
+ * w = n * (alpha - chi2 / beta), the "normalized" chi2 of the whole track read as chi2 per
+ * degree of freedom, ndf = 2 n - 5 (two measured coordinates per cluster, five fitted
+ * parameters).  A tracklet with ndf < 1 has no weight and claims no cluster. */
+static real tracklet_weight(int n, real chi2sum, real alpha, real beta)
+{
+    int ndf = 2 * n - 5;
+    if (ndf < 1) return (real)-INFINITY;
+    return (real)n * (alpha - (chi2sum / (real)ndf) / beta);
+}
+
+/* Section 3.1: every cluster goes to the tracklet of largest weight among those holding it;
+ * of equal weights the earlier tracklet (lower index) keeps it.  Tracklets t0 .. t0 + T - 1,
+ * hits[t * nr ..] their clusters, weights wv[t]; owner[c] is -1 for a cluster nobody claimed. */
+static void claim_clusters(int64_t t0, int64_t T, const int32_t *nhits, const int32_t *hits, int nr,
+                           const real *wv, int32_t *owner)
+{
+    for (int64_t i = 0; i < T; i++) {
+        int64_t t = t0 + i;
+        if (wv[t] == (real)-INFINITY) continue;
+        const int32_t *h = hits + (size_t)t * (size_t)nr;
+        for (int j = 0; j < nhits[t]; j++) {
+            int32_t c = h[j];
+            int32_t o = owner[c];
+            if (o < 0 || wv[t] > wv[o]) owner[c] = (int32_t)t;
+        }
+    }
+}
+
 /* A5 tracklet construction for the tracklet starting at cluster c0 (Section 1,
  * "Tracklet construction"): seed from the chain, fit outwards while searching each
  * row, then refit inwards from the outermost cluster with a fresh covariance. */
@@ -600,11 +629,7 @@ static void construct(Sector *S, const K *k, const real *Y, const real *Zc, cons
         for (int j = 0; j <= i; j++) res->tl_cov[t * 15 + q++] = (double)inner.C[i][j];
     res->tl_x[t] = (double)xin;
     res->tl_chi2[t] = (double)chi2sum;
-    if (ndf >= 1) {
-        /* Section 3.1: w = n * (alpha - chi2/beta), chi2 read as chi2 per degree of freedom */
-        real w = (real)n * (k->alpha - (chi2sum / (real)ndf) / k->beta);
-        res->tl_w[t] = (double)w;
-    }
+    res->tl_w[t] = (double)tracklet_weight(n, chi2sum, k->alpha, k->beta);
 }
 
 /* A6 selection and A7 output order for one sector. */
@@ -612,17 +637,7 @@ static void sector_select(Sector *S, const K *k, orc_result *res, int64_t t0, co
 {
     int nr = k->nr;
     int64_t T = S->nstarts;
-    /* each cluster goes to the tracklet of maximal weight; equal weights: the earlier tracklet */
-    for (int64_t i = 0; i < T; i++) {
-        int64_t t = t0 + i;
-        if (res->tl_ndf[t] < 1) continue;
-        const int32_t *h = res->tl_hits + (size_t)t * (size_t)nr;
-        for (int j = 0; j < res->tl_nhits[t]; j++) {
-            int32_t c = h[j];
-            int32_t o = res->owner[c];
-            if (o < 0 || wv[t] > wv[o]) res->owner[c] = (int32_t)t;
-        }
-    }
+    claim_clusters(t0, T, res->tl_nhits, res->tl_hits, nr, wv, res->owner);
     int64_t *keys = (int64_t *)malloc(sizeof(int64_t) * 2 * (size_t)(T > 0 ? T : 1));
     int64_t na = 0;
     for (int64_t i = 0; i < T; i++) {
@@ -1410,3 +1425,19 @@ void orc_bin_row_f32(const double *y, const double *z, int n, float ymin, float 
     free(fill);
 }
 #endif
+
+/* Section 3.1 as the tracker applies it, for pins: weights of T tracklets from their cluster
+ * counts and fit chi2 (in working precision), then the owner of each of n_clusters clusters
+ * (hits: [T * n_rows], the first nhits[t] entries of row t used). */
+void SFX(orc_select)(int64_t T, const int32_t *nhits, const double *chi2, const int32_t *hits, int n_rows,
+                     double alpha, double beta, int64_t n_clusters, double *w_out, int32_t *owner_out)
+{
+    real *wv = (real *)malloc(sizeof(real) * (size_t)(T > 0 ? T : 1));
+    for (int64_t t = 0; t < T; t++) {
+        wv[t] = tracklet_weight(nhits[t], (real)chi2[t], (real)alpha, (real)beta);
+        w_out[t] = (double)wv[t];
+    }
+    for (int64_t c = 0; c < n_clusters; c++) owner_out[c] = -1;
+    claim_clusters(0, T, nhits, hits, n_rows, wv, owner_out);
+    free(wv);
+}

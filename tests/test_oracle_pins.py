@@ -415,3 +415,18 @@ def test_float_arcsin_series_accuracy():
         assert r == oracle.asin_ratio_f32(float(-x))
     assert worst <= 3 * np.finfo(np.float32).eps, worst
     assert oracle.asin_ratio_f32(0.0) == 1.0
+
+
+def test_float_mode_error_against_double_mode():
+    """The float reading of the tracker against the double one on the 36-sector workload (4000
+    tracks): concordance and mean relative parameter error per component within ten times the
+    values measured for the float GPU path (which equals the float mode), scales 1 cm, 1 cm, 1e-3,
+    1e-3, 1e-2 e/GeV."""
+    from paper_1712_09407_gb300 import concordance
+    ev = eg.config_event(1)
+    cfg = oracle.config_for(ev.geometry)
+    r32 = oracle.track_event(cfg, ev.y, ev.z, ev.row, ev.counts, precision=32)
+    r64 = oracle.track_event(cfg, ev.y, ev.z, ev.row, ev.counts, precision=64)
+    c = concordance.compare(concordance.oracle_tracks(r64), concordance.oracle_tracks(r32), ev.n)
+    assert c["concordance"] >= 0.9999, c["concordance"]
+    assert np.all(c["par_rel_mean"] <= np.array([8.8e-6, 1.8e-6, 9.9e-5, 8.1e-6, 3.5e-5])), c["par_rel_mean"]
