@@ -150,14 +150,19 @@ def test_a7_tracks(both1):
     assert np.all(out["nhits"] >= 30)
 
 
+FP64_MEAN_REL_GATE = np.array([8.8e-6, 1.8e-6, 9.9e-5, 8.1e-6, 3.5e-5])
+
+
 def test_error_against_fp64_oracle(both1):
     """States the per-parameter error of the float GPU path against the double oracle."""
     ev, out, dbg, ref = both1
     ref64 = run_oracle(ev, precision=64, key="c1")
     c = compare_tracks(ev, out, ref64)
     print("vs FP64: concordance %.7f mean rel %s max rel %s" % (c["concordance"], c["par_rel_mean"], c["par_rel_max"]))
-    assert c["concordance"] >= 0.999
-    assert np.all(c["par_rel_mean"] < 1e-3)
+    # gates at ten times the measured mean relative errors (y, z, sin phi, tan lambda, q/pT with
+    # scales 1 cm, 1 cm, 1e-3, 1e-3, 1e-2: 8.8e-7, 1.8e-7, 9.9e-6, 8.1e-7, 3.5e-6)
+    assert c["concordance"] >= 0.9999
+    assert np.all(c["par_rel_mean"] <= FP64_MEAN_REL_GATE), c["par_rel_mean"]
 
 
 # ---------------------------------------------------------------------------------------------
