@@ -10,19 +10,23 @@ value: one step = one call tracking --events-per-call (3) central-like events in
 of every stage (tpc_track_batch); --inflight (2) calls are on the device at once, each on
 its own tracker and stream, as a stream of events is served.  Inputs (12 distinct events,
 more than L2 together) are resident in HBM before the timed region, which is bracketed by
-CUDA events on the streams; value = events / device time.  Beside it in the same line:
-the same stream with one event per call, one event at a time with L2 flushed before each
-(latency, per-stage times and the constructor's roofline), the optional stages, and the
-end-to-end figure from pinned host buffers through tpc_track_batch_host with the results
-copied back.
+CUDA events on the streams; value = events / device time.  Every tracker's workspace and
+result buffers are allocated before timing (tpc_tracker_reserve, tpc_tracker_reserve_results)
+and the warm-up runs the timed pattern itself, so the timed calls allocate nothing and the
+value does not depend on --steps; Python's garbage collector is off while a region is timed.  Beside it in the same line: the same stream with one event
+per call, one event at a time with L2 flushed before each (latency), the step's call alone
+(per-stage times and the per-stage and total rooflines), the optional stages, the end-to-end
+figure from pinned host buffers through tpc_track_batch_host with the results copied back,
+and Poisson-arrival serving latency through the native serving loop.
 
 Prints one JSON line (rank 0).  ``--impl reference`` times the CPU oracle (the reference
-arm of this build) on the host cores instead.
+arm of this build) on the host cores, on the same resident events.
 """
 from __future__ import annotations
 
 import argparse
 import collections
+import gc
 import hashlib
 import json
 import os
@@ -47,11 +51,14 @@ CONSTRUCT_SRC = [os.path.join(ROOT, "paper_1712_09407_gb300", "csrc", f) for f i
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=400)
-    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--steps", type=int, default=100)
+    ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-serving", action="store_true")
+    ap.add_argument("--serve-seconds", type=float, default=10.0, help="length of each serving run")
+    ap.add_argument("--serve-pool", type=int, default=32, help="events of the batched workload the arrivals draw from")
     ap.add_argument("--workload", default="central", choices=["central", "batch"],
                     help="central: the metric's workload (default); batch: 64 events per call vs one at a time")
     ap.add_argument("--batch-events", type=int, default=64)
@@ -152,11 +159,56 @@ def measured_peaks():
     return 6800.0, "fallback"
 
 
-def construct_bytes(stats):
-    """Algorithmic bytes of one tracklet-construction launch (A5): per row visit 16 B unit metadata + 8 B grid size + 16 B grid origin/scale + 8 B per
-    z-row of cells (2 cell starts) + 8 B per cluster read from the cells; per tracklet a
-    16 B start record, three 8 B seed points, 4 B input index, 100 B of results and 4 B per
-    fitted cluster (taken as 2 per visit of the inward pass, bounded by the visit count)."""
+# Algorithmic bytes of each stage per work unit: every stage reads its inputs and writes its
+# outputs once.  N clusters, T tracklets, V construction row visits, K candidates read in them,
+# Htl clusters of the claiming tracklets, H output hits, M output tracks.
+STAGE_BYTES = {
+    "ingest": ("25 B per cluster (9 B in, 12 B sorted out, 4 B bin key)", lambda u: 25 * u["N"]),
+    "neighbours": ("32 B per cluster (8 B own, 16 B rows k+-1, 8 B links)", lambda u: 32 * u["N"]),
+    "evolution": ("24 B per cluster + 4 B per tracklet", lambda u: 24 * u["N"] + 4 * u["T"]),
+    "construction": ("(12 + 8 k) B per row visit (k candidates per visit) + 100 B per tracklet",
+                     lambda u: 12 * u["V"] + 8 * u["K"] + 100 * u["T"]),
+    "selection": ("20 B per tracklet cluster (8 B atomic, 8 B re-read, 4 B index)", lambda u: 20 * u["Htl"]),
+    "output": ("4 B per kept hit + 100 B per track", lambda u: 4 * u["H"] + 100 * u["M"]),
+}
+STAGE_INDEX = {"ingest": 1, "neighbours": 2, "evolution": 3, "construction": 4, "selection": 5, "output": 6}
+
+
+def units_of(stats):
+    """Work units of one call from its counters (tpc_result_stats)."""
+    return dict(N=int(stats["clusters"]), T=int(stats["tracklets"]), V=int(stats["row_visits"]),
+                K=int(stats["candidates"]), Htl=int(stats["tracklet_hits"]), H=int(stats["hits"]),
+                M=int(stats["tracks"]))
+
+
+def stage_roofline(units, stage_ms, call_ms, peak):
+    """Algorithmic bytes / CUDA-event time of each stage against the HBM peak, the whole path's
+    total, and the compulsory input/output traffic as a lower bound."""
+    stages, tot_b, tot_ms = {}, 0, 0.0
+    for name, (formula, f) in STAGE_BYTES.items():
+        b = int(f(units))
+        ms = float(stage_ms[STAGE_INDEX[name]])
+        gbs = b / (ms * 1e-3) / 1e9 if ms > 0 else None
+        stages[name] = {"bytes": b, "ms": round(ms, 4), "achieved_gbs": gbs,
+                        "frac": gbs / peak if gbs else None, "per_unit": formula}
+        tot_b += b
+        tot_ms += ms
+    compulsory = 9 * units["N"] + 4 * units["H"] + 112 * units["M"]
+    total = {"bytes": tot_b, "ms_stages": round(tot_ms, 4), "achieved_gbs": tot_b / (tot_ms * 1e-3) / 1e9,
+             "frac": tot_b / (tot_ms * 1e-3) / 1e9 / peak, "ms_call": round(call_ms, 4),
+             "frac_of_call": tot_b / (call_ms * 1e-3) / 1e9 / peak,
+             "bytes_per_cluster": tot_b / max(1, units["N"])}
+    comp = {"bytes": compulsory, "bytes_per_cluster": compulsory / max(1, units["N"]),
+            "what": "9 B per input cluster in, 4 B per output hit + 112 B per output track out",
+            "frac_of_call": compulsory / (call_ms * 1e-3) / 1e9 / peak}
+    return stages, total, comp
+
+
+def construct_bytes_touched(stats):
+    """Bytes the constructor's loads and stores touch (a wider model than the algorithmic bytes
+    above, kept beside them): per row visit 16 B unit record + 8 B grid size + 16 B grid
+    origin/scale + 8 B per z-row of cells + 2 B of fitted-cluster index, 8 B per candidate read, per
+    tracklet 16 B start record, three 8 B seed points, 4 B input index and 100 B of results."""
     V, K, T = stats["row_visits"], stats["candidates"], stats["tracklets"]
     return V * (16 + 8 + 16 + 8) + 8 * K + T * (16 + 24 + 4 + 100) + 4 * V // 2
 
@@ -187,6 +239,22 @@ def traffic_for_current_kernel():
 
 
 # ------------------------------------------------------------------------------------------------
+# workload (identical in both arms)
+# ------------------------------------------------------------------------------------------------
+def workload_config(n_resident, n_mean, world):
+    return {"workload": WORKLOAD, "resident_events": n_resident, "clusters_per_event": int(round(n_mean)),
+            "event_seeds": "(1, %d) .. (1, %d)" % (0, n_resident - 1),
+            "l2": "inputs larger than L2 (%d resident events, %.0f MB); no flush" % (n_resident, n_resident * n_mean * 9 / 1e6),
+            "parallelism": "replicas" if world > 1 else "single GPU"}
+
+
+def resident_events(n, first_event, pin):
+    """The resident central-like events (about 30 MB each), generated in parallel."""
+    from paper_1712_09407_gb300.serving import event_pool
+    return event_pool(n, cfg=2, first_event=first_event, pin=pin)
+
+
+# ------------------------------------------------------------------------------------------------
 # CPU oracle legs
 # ------------------------------------------------------------------------------------------------
 def cpu_model() -> str:
@@ -208,55 +276,61 @@ def cpu_model() -> str:
     return platform.machine()
 
 
-def oracle_timing(ev, min_seconds=10.0, max_runs=60, min_runs=1):
-    """The float-mode oracle on the host cores (OpenMP over the 36 sectors), then once on one
-    thread (a bounded sample: one event)."""
+def oracle_steps(pool, n_steps, max_seconds, cfg=None):
+    """The float-mode oracle over the resident events in turn (OpenMP over the 36 sectors):
+    at most n_steps events and about max_seconds of CPU time.  Returns (events, seconds)."""
     import oracle
-    cfg = oracle.config_for(ev.geometry)
-    times = []
-    t_total = time.perf_counter()
-    while len(times) < max_runs and (len(times) < min_runs or time.perf_counter() - t_total < min_seconds):
-        t0 = time.perf_counter()
-        oracle.track_event(cfg, ev.y, ev.z, ev.row, ev.counts, precision=32)
-        times.append(time.perf_counter() - t0)
-    cores = os.cpu_count()
+    from paper_1712_09407_gb300 import eventgen
+    cfg = cfg or oracle.config_for(eventgen.Geometry())
     t0 = time.perf_counter()
-    oracle.track_event(oracle.config_for(ev.geometry, n_threads=1), ev.y, ev.z, ev.row, ev.counts, precision=32)
+    k = 0
+    while k < n_steps and (k == 0 or time.perf_counter() - t0 < max_seconds):
+        y, z, row, counts, _ = pool[k % len(pool)]
+        oracle.track_event(cfg, y.numpy(), z.numpy(), row.numpy(), counts, precision=32)
+        k += 1
+    return k, time.perf_counter() - t0
+
+
+def oracle_timing(pool, seconds=12.0):
+    """The oracle on the host cores over the resident events (a bounded sample), then one event
+    on one thread."""
+    import oracle
+    from paper_1712_09407_gb300 import eventgen
+    oracle_steps(pool, 1, 0.0)                                  # first call: page-in, thread start-up
+    k, dt = oracle_steps(pool, 10 ** 6, seconds)
+    cores = os.cpu_count()
+    y, z, row, counts, n = pool[0]
+    t0 = time.perf_counter()
+    oracle.track_event(oracle.config_for(eventgen.Geometry(), n_threads=1), y.numpy(), z.numpy(), row.numpy(),
+                       counts, precision=32)
     t_one = time.perf_counter() - t0
-    return dict(value=len(times) / sum(times), unit="events/s", cores=cores, kind="oracle",
-                sample="full central-like event (3.29 M clusters), float-mode C oracle, OpenMP over the 36 "
-                       "sectors on %d threads, %d runs, %.1f s" % (cores, len(times), sum(times)),
+    return dict(value=k / dt, unit="events/s", cores=cores, kind="oracle",
+                sample="%d of the resident central-like events in turn (float-mode C oracle, OpenMP over the 36 "
+                       "sectors on %d threads), %.1f s" % (k, cores, dt),
                 single_thread={"value": 1.0 / t_one, "unit": "events/s", "sample": "one event on one thread"},
                 cpu_model=cpu_model())
 
 
 def run_reference(args):
+    """The reference arm: the CPU oracle on the same resident events as our arm, one event per step."""
     rank, world, _ = dist_env()
     if rank != 0:
         return 0
-    from paper_1712_09407_gb300 import eventgen
     import oracle
     oracle.build()
-    ev = eventgen.config_event(2)
-    cfg = oracle.config_for(ev.geometry)
-    for _ in range(args.warmup):
-        oracle.track_event(cfg, ev.y, ev.z, ev.row, ev.counts, precision=32)
-    # at most --steps events and about a minute of CPU time
-    t0 = time.perf_counter()
-    steps = 0
-    while steps < args.steps and (steps == 0 or time.perf_counter() - t0 < 60.0):
-        oracle.track_event(cfg, ev.y, ev.z, ev.row, ev.counts, precision=32)
-        steps += 1
-    dt = time.perf_counter() - t0
+    pool = resident_events(args.resident, 0, pin=False)
+    n_mean = float(np.mean([p[4] for p in pool]))
+    oracle_steps(pool, max(1, args.warmup), 1e9)
+    steps, dt = oracle_steps(pool, args.steps, 90.0)
     v = steps / dt
     cores = os.cpu_count()
     line = {"impl": "reference", "metric": METRIC, "value": v, "unit": "events/s", "n_gpus": args.gpus,
             "steps": steps, "warmup": args.warmup, "ms_per_step": dt * 1e3 / steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
-            "data": "synthetic", "config": {"workload": WORKLOAD, "clusters_per_event": ev.n},
+            "data": "synthetic", "config": workload_config(len(pool), n_mean, world),
             "cpu_baseline": {"value": v, "unit": "events/s", "cores": cores, "kind": "oracle",
-                             "sample": "full central-like event per step, float-mode C oracle, OpenMP over "
-                                       "36 sectors on %d host threads" % cores},
+                             "sample": "%d of the resident central-like events in turn, one per step, float-mode "
+                                       "C oracle, OpenMP over 36 sectors on %d host threads" % (steps, cores)},
             "e2e": {"value": v, "unit": "events/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line))
     return 0
@@ -265,6 +339,64 @@ def run_reference(args):
 # ------------------------------------------------------------------------------------------------
 # our arm
 # ------------------------------------------------------------------------------------------------
+QDEPTH = 6     # calls each tracker has outstanding in the streamed legs (its result ring holds one more)
+STAGES = ["setup", "ingest", "neighbours", "evolution", "construction", "selection", "output", "global", "merge"]
+
+
+class Streamer:
+    """A stream of tracker calls round-robin over trackers, one CUDA stream each, keeping QDEPTH
+    calls per tracker outstanding (the oldest is retired on the host while the device works)."""
+
+    def __init__(self, torch, trackers, streams, world):
+        self.torch, self.trackers, self.streams, self.world = torch, trackers, streams, world
+
+    def barrier(self):
+        self.torch.cuda.synchronize()
+        if self.world > 1:
+            self.torch.distributed.barrier()
+        self.torch.cuda.synchronize()
+
+    def run(self, n_calls, submit, timed):
+        torch = self.torch
+        nt = len(self.trackers)
+        gc_was = gc.isenabled()
+        gc.disable()                   # no collector pause may starve the device queue while timing
+        launches, tracks = 0, []
+        start = ends = None
+        if timed:
+            self.barrier()
+            start = torch.cuda.Event(enable_timing=True)
+            ends = [torch.cuda.Event(enable_timing=True) for _ in self.streams]
+            start.record(self.streams[0])
+            for s_ in self.streams[1:]:
+                s_.wait_event(start)
+        pend = collections.deque()
+
+        def retire(r):
+            nonlocal launches
+            r.sync()
+            launches += r.stats()["kernel_launches"]
+            tracks.append(r.n_tracks)
+            r.release()
+
+        for k in range(n_calls):
+            i = k % nt
+            with torch.cuda.stream(self.streams[i]):
+                pend.append(submit(self.trackers[i], k, self.streams[i]))
+            if len(pend) > nt * QDEPTH:
+                retire(pend.popleft())
+        if timed:
+            for e, s_ in zip(ends, self.streams):
+                e.record(s_)
+        self.barrier()
+        while pend:
+            retire(pend.popleft())
+        total_s = max(start.elapsed_time(e) for e in ends) / 1e3 if timed else None
+        if gc_was:
+            gc.enable()
+        return total_s, launches, tracks
+
+
 def run_ours(args):
     import torch
 
@@ -278,14 +410,10 @@ def run_ours(args):
     from paper_1712_09407_gb300 import eventgen
     from paper_1712_09407_gb300.tracker import Tracker
 
-    # Resident inputs: `resident` different central-like events (about 30 MB each, together more
-    # than the 129 MB L2), generated in parallel, copied to HBM before any timing.
-    from paper_1712_09407_gb300.serving import event_pool
-    first_event = replica_event(rank) * args.resident
-    pool = event_pool(args.resident, cfg=2, first_event=first_event)
-    import types
-    ev = types.SimpleNamespace(geometry=eventgen.Geometry(), y=pool[0][0].numpy(), z=pool[0][1].numpy(),
-                               row=pool[0][2].numpy(), counts=pool[0][3], n=pool[0][4])   # first resident event
+    # Resident inputs: `resident` different central-like events (together more than the 129 MB L2),
+    # copied to HBM before any timing; rank r tracks its own events (replicas)
+    pool = resident_events(args.resident, replica_event(rank) * args.resident, pin=True)
+    geo = eventgen.Geometry()
     dev = [(p[0].cuda(), p[1].cuda(), p[2].cuda(), p[3], p[4]) for p in pool]
     n_mean = float(np.mean([p[4] for p in pool]))
     # calls of B consecutive resident events (inputs concatenated on the device and, for the
@@ -299,354 +427,311 @@ def run_ours(args):
                           row=torch.cat([d[2] for d in ds]), counts=np.concatenate([p[3] for p in ps]),
                           n=sum(p[4] for p in ps), hy=torch.cat([p[0] for p in ps]).pin_memory(),
                           hz=torch.cat([p[1] for p in ps]).pin_memory(), hr=torch.cat([p[2] for p in ps]).pin_memory()))
-    trackers = [Tracker.for_geometry(ev.geometry) for _ in range(args.inflight)]
+    # B-event calls and one-event calls on separate trackers (each keeps one executable graph); every
+    # tracker's workspace and result buffers are allocated here, so the timed calls allocate nothing
+    trackers = [Tracker.for_geometry(geo) for _ in range(args.inflight)]
     for t in trackers:
-        t.reserve(max(c_["n"] for c_ in calls), B)
-    tr = trackers[0]
+        t.reserve(max(c_["n"] for c_ in calls), B, results=QDEPTH + 1)
+    trackers1 = [Tracker.for_geometry(geo) for _ in range(args.inflight)]
+    for t in trackers1:
+        t.reserve(max(p[4] for p in pool), 1, results=QDEPTH + 1)
     streams = [torch.cuda.Stream() for _ in range(args.inflight)]
     stream = streams[0]
     flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
     torch.cuda.synchronize()
 
-    def call(t, c_, s_):
+    def call_b(t, k, s_):
+        c_ = calls[k % len(calls)]
         if B == 1:
             return t.track(c_["y"], c_["z"], c_["row"], c_["counts"], stream=s_)
         return t.track_batch(c_["y"], c_["z"], c_["row"], c_["counts"], B, stream=s_)
 
-    for i, t in enumerate(trackers):
-        with torch.cuda.stream(streams[i]):
-            for k in range(args.warmup):
-                r = call(t, calls[k % len(calls)], streams[i])
-                r.sync()
-                r.release()
-                d = dev[k % len(dev)]
-                r = t.track(d[0], d[1], d[2], d[3], stream=streams[i])
-                r.sync()
-                r.release()
+    def call_1(t, k, s_):
+        d = dev[k % len(dev)]
+        return t.track(d[0], d[1], d[2], d[3], stream=s_)
 
-    def barrier():
-        torch.cuda.synchronize()
-        if world > 1:
-            torch.distributed.barrier()
-        torch.cuda.synchronize()
+    sb = Streamer(torch, trackers, streams, world)
+    s1 = Streamer(torch, trackers1, streams, world)
+    # warm-up: the timed pattern itself (same trackers, streams, call shape and depth of outstanding
+    # calls), so that graphs, staging buffers and result buffers are all in use before timing
+    n_warm = max(args.warmup, args.inflight * (QDEPTH + 2))
+    sb.run(n_warm, call_b, timed=False)
+    s1.run(n_warm, call_1, timed=False)
 
-    # ---- timed region 1 (the value): a stream of calls of B central-like events each, `inflight`
-    # calls on the device at once (one tracker and stream each), inputs larger than L2 so no flush
-    # is needed.  Per-call stage timing stays off here (its event records would be part of every
-    # call); the stage times come from the one-at-a-time regions below.
+    # ---- timed region (the value): a stream of calls of B central-like events each, `inflight` calls
+    # on the device at once (one tracker and stream each); per-call stage timing stays off here
     clocks = ClockSampler(local)
     clocks.start()
-    barrier()
     t_wall = time.perf_counter()
-    t_start = torch.cuda.Event(enable_timing=True)
-    t_ends = [torch.cuda.Event(enable_timing=True) for _ in streams]
-    t_start.record(streams[0])
-    for s_ in streams[1:]:
-        s_.wait_event(t_start)
-    results = collections.deque()
-    launches = 0
-    tracks = []
-
-    def retire(r):
-        nonlocal launches
-        r.sync()                                       # host waits on an older call; the device keeps going
-        launches += r.stats()["kernel_launches"]
-        tracks.append(r.n_tracks)
-        r.release()
-
-    for k in range(args.steps):
-        i = k % args.inflight
-        with torch.cuda.stream(streams[i]):
-            results.append(call(trackers[i], calls[k % len(calls)], streams[i]))
-        if len(results) > 4 * args.inflight:
-            retire(results.popleft())
-    for e, s_ in zip(t_ends, streams):
-        e.record(s_)
-    barrier()
+    total_s, launches, tracks = sb.run(args.steps, call_b, timed=True)
     wall = time.perf_counter() - t_wall
     clk = clocks.stop()
-    while results:
-        retire(results.popleft())
-    total_s = reduce_max(max(t_start.elapsed_time(e) for e in t_ends) / 1e3, world, "cuda")
+    total_s = reduce_max(total_s, world, "cuda")
     value = replica_throughput(total_s, args.steps * B, world)
 
     # the same stream with one event per call (tpc_track_event), for comparison
-    n_one = min(args.steps * B, 400)
-    o_start = torch.cuda.Event(enable_timing=True)
-    o_ends = [torch.cuda.Event(enable_timing=True) for _ in streams]
-    barrier()
-    o_start.record(streams[0])
-    for s_ in streams[1:]:
-        s_.wait_event(o_start)
-    pend = collections.deque()
-    for k in range(n_one):
-        i = k % args.inflight
-        d = dev[k % len(dev)]
-        with torch.cuda.stream(streams[i]):
-            pend.append(trackers[i].track(d[0], d[1], d[2], d[3], stream=streams[i]))
-        if len(pend) > 4 * args.inflight:
-            r = pend.popleft()
-            r.sync()
-            r.release()
-    for e, s_ in zip(o_ends, streams):
-        e.record(s_)
-    barrier()
-    while pend:
-        r = pend.popleft()
-        r.sync()
-        r.release()
-    one_call_s = reduce_max(max(o_start.elapsed_time(e) for e in o_ends) / 1e3, world, "cuda")
-    one_per_call = {"events_per_s": replica_throughput(one_call_s, n_one, world), "events": n_one,
+    n_one = max(args.steps * B, 3 * args.inflight * QDEPTH)
+    one_s, _, _ = s1.run(n_one, call_1, timed=True)
+    one_s = reduce_max(one_s, world, "cuda")
+    one_per_call = {"events_per_s": replica_throughput(one_s, n_one, world), "events": n_one,
                     "inflight_calls": args.inflight, "path": "tpc_track_event, one event per call"}
 
-    # ---- timed region 2 (per-event latency and the per-kernel roofline): one event at a time on
-    # one stream, L2 flushed (untimed) before each step
-    for t in trackers:
-        t.set_timing(True)
-    n_serial = min(args.steps, 40)
+    # ---- one event at a time on one stream, L2 flushed (untimed) before each: latency and stages
+    tr1 = trackers1[0]
+    tr1.set_timing(True)
+    n_serial = min(max(args.steps, 10), 40)
     starts = [torch.cuda.Event(enable_timing=True) for _ in range(n_serial)]
     ends = [torch.cuda.Event(enable_timing=True) for _ in range(n_serial)]
     stage_ms = np.zeros(9)
     stats_all = []
-    results = []
-    barrier()
+    sb.barrier()
     with torch.cuda.stream(stream):
         for k in range(n_serial):
-            d = dev[k % len(dev)]
             flush.fill_(float(k))
             starts[k].record(stream)
-            results.append(tr.track(d[0], d[1], d[2], d[3], stream=stream))
+            r = call_1(tr1, k, stream)
             ends[k].record(stream)
-    barrier()
-    for r in results:
-        r.sync()
-        st = r.stats()
-        stats_all.append(st)
-        stage_ms += np.array(st["ms"])
-        r.release()
-    del results
+            r.sync()
+            st = r.stats()
+            stats_all.append(st)
+            stage_ms += np.array(st["ms"])
+            r.release()
     step_ms = [s.elapsed_time(e) for s, e in zip(starts, ends)]
     serial = {"events_per_s": n_serial / (sum(step_ms) / 1e3), "ms_per_event": float(np.mean(step_ms)), "steps": n_serial,
               "ms_per_event_p50": float(np.median(step_ms)), "l2": "flushed before every event (512 MB write, untimed)"}
-    # the step's own call (B events) one at a time, L2 flushed before each: the constructor's
-    # roofline is taken on it
-    n_bs = min(args.steps, 12)
+    tr1.set_timing(False)
+    # the step's own call (B events) one at a time, L2 flushed before each: stage times and rooflines
+    trb = trackers[0]
+    trb.set_timing(True)
+    n_bs = min(max(args.steps, 6), 12)
     b_stats, b_ms = [], []
-    barrier()
     with torch.cuda.stream(stream):
-        for k in range(n_bs):
+        for k in range(n_bs + 1):
             flush.fill_(float(k))
             a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
             a.record(stream)
-            r = call(tr, calls[k % len(calls)], stream)
+            r = call_b(trb, k, stream)
             b.record(stream)
             r.sync()
-            b_stats.append(r.stats())
+            if k > 0:                        # the first call builds the timed graph
+                b_stats.append(r.stats())
+                b_ms.append(a.elapsed_time(b))
             r.release()
-            b_ms.append(a.elapsed_time(b))
+    trb.set_timing(False)
     b_stage = np.mean([np.array(s_["ms"]) for s_ in b_stats], axis=0)
-    stats = {k: int(np.mean([s_[k] for s_ in b_stats])) for k in ("row_visits", "candidates", "tracklets")}
-    for t in trackers:
-        t.set_timing(False)
+    b_units = {k: int(np.mean([units_of(s_)[k] for s_ in b_stats])) for k in units_of(b_stats[0])}
 
-    # ---- global tracking (Section 5) on the same events, one at a time, L2 flushed (untimed)
+    # ---- optional stages on the same events, one at a time, L2 flushed (untimed)
     def extra_pass(**flags):
-        """The same events one at a time with global tracking and/or the merger on."""
-        xtr = Tracker.for_geometry(ev.geometry, **flags)
-        xtr.reserve(max(p[4] for p in pool), 1)
-        n_x = min(args.steps, 20)
+        xtr = Tracker.for_geometry(geo, **flags)
+        xtr.reserve(max(p[4] for p in pool), 1, results=2)
+        n_x = min(max(args.steps, 10), 20)
         x_ms, x_stats = [], []
         with torch.cuda.stream(stream):
             for k in range(args.warmup):
-                d = dev[k % len(dev)]
-                r = xtr.track(d[0], d[1], d[2], d[3], stream=stream)
+                r = call_1(xtr, k, stream)
                 r.sync()
                 r.release()
             xtr.set_timing(True)
-            for k in range(n_x):
-                d = dev[k % len(dev)]
+            for k in range(n_x + 1):
                 flush.fill_(float(k))
                 a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
                 a.record(stream)
-                r = xtr.track(d[0], d[1], d[2], d[3], stream=stream)
+                r = call_1(xtr, k, stream)
                 b.record(stream)
                 r.sync()
-                x_stats.append(r.stats())
+                if k > 0:
+                    x_stats.append(r.stats())
+                    x_ms.append(a.elapsed_time(b))
                 r.release()
-                x_ms.append(a.elapsed_time(b))
         xtr.close()
         st_ms = np.mean([np.array(s_["ms"]) for s_ in x_stats], axis=0)
         return n_x, x_ms, x_stats, st_ms
 
-    gtr = Tracker.for_geometry(ev.geometry, global_tracking=True)
-    gtr.reserve(max(p[4] for p in pool), 1)
-    n_g = min(args.steps, 20)
-    g_ms, g_stats = [], []
-    with torch.cuda.stream(stream):
-        for k in range(args.warmup):
-            d = dev[k % len(dev)]
-            r = gtr.track(d[0], d[1], d[2], d[3], stream=stream)
-            r.sync()
-            r.release()
-        gtr.set_timing(True)
-        for k in range(n_g):
-            d = dev[k % len(dev)]
-            flush.fill_(float(k))
-            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-            a.record(stream)
-            r = gtr.track(d[0], d[1], d[2], d[3], stream=stream)
-            b.record(stream)
-            r.sync()
-            g_stats.append(r.stats())
-            r.release()
-            g_ms.append(a.elapsed_time(b))
-    gtr.close()
-    g_stage = np.mean([np.array(s_["ms"]) for s_ in g_stats], axis=0)
+    n_g, g_ms, g_stats, g_stage = extra_pass(global_tracking=True)
+    plain_hits = {k % len(dev): stats_all[k]["hits"] for k in range(n_serial)}     # event -> hits without
+    added = [g_stats[j]["hits"] - plain_hits[(j + 1) % len(dev)] for j in range(n_g) if (j + 1) % len(dev) in plain_hits]
     global_line = {
         "events_per_s": n_g / (sum(g_ms) / 1e3), "ms_per_event": float(np.mean(g_ms)), "steps": n_g,
-        "stages_ms": {n: round(float(v), 4) for n, v in zip(
-            ["setup", "ingest", "neighbours", "evolution", "construction", "selection", "output", "global", "merge"], g_stage)},
+        "stages_ms": {n: round(float(v), 4) for n, v in zip(STAGES, g_stage)},
         "clusters_found_per_event": float(np.mean([s_["global_found"] for s_ in g_stats])),
-        "clusters_added_per_event": float(np.mean([g_stats[k]["hits"] - stats_all[k]["hits"] for k in range(n_g)])),
+        "clusters_added_per_event": float(np.mean(added)) if added else None,
         "tracks_per_event": float(np.mean([s_["tracks"] for s_ in g_stats])),
         "l2": "flushed before every event (512 MB write, untimed)"}
     n_m, m_ms, m_stats, m_stage = extra_pass(global_tracking=True, merge=True)
     merge_line = {
         "what": "global tracking + track merger with refit",
         "events_per_s": n_m / (sum(m_ms) / 1e3), "ms_per_event": float(np.mean(m_ms)), "steps": n_m,
-        "stages_ms": {n: round(float(v), 4) for n, v in zip(
-            ["setup", "ingest", "neighbours", "evolution", "construction", "selection", "output", "global", "merge"],
-            m_stage)},
+        "stages_ms": {n: round(float(v), 4) for n, v in zip(STAGES, m_stage)},
         "sector_tracks_per_event": float(np.mean([s_["sector_tracks"] for s_ in m_stats])),
         "merged_tracks_per_event": float(np.mean([s_["tracks"] for s_ in m_stats])),
         "l2": "flushed before every event (512 MB write, untimed)"}
 
-    # ---- end to end through the host-buffer entry point: every step copies its event from pinned
-    # host memory, tracks it and copies the result back (all inside the timed region); two events
-    # are in flight on two trackers and streams, as a user keeps them, and the one-at-a-time
-    # figure is kept beside it
+    # ---- end to end through the host-buffer entry point: every call copies its events from pinned
+    # host memory, tracks them and copies the result back (all inside the timed region), `inflight`
+    # calls in flight on their trackers and streams; the one-event-at-a-time figure beside it
     e2e = None
     if not args.no_e2e:
-        from paper_1712_09407_gb300.tracker import tpc_result_copy_to_host
+        e2e = e2e_leg(args, torch, pool, calls, trackers, streams, tr1, stream, flush, B, world)
 
-        def host_bufs(bufs, M, H):
-            if bufs is None or bufs["par"].shape[0] < M or bufs["hits"].shape[0] < H:
-                bufs = dict(par=torch.empty((M + 1024, 5)).pin_memory(), cov=torch.empty((M + 1024, 15)).pin_memory(),
-                            x_ref=torch.empty(M + 1024).pin_memory(), alpha=torch.empty(M + 1024).pin_memory(),
-                            chi2=torch.empty(M + 1024).pin_memory(),
-                            **{n: torch.empty(M + 1024, dtype=torch.int32).pin_memory()
-                               for n in ("ndf", "nhits", "first", "sector", "event")},
-                            hits=torch.empty(H + 65536, dtype=torch.int32).pin_memory())
-            return bufs
-
-        # one at a time
-        hy, hz, hr = pool[0][0], pool[0][1], pool[0][2]          # pinned host copies
-        bufs = None
-        times = []
-        with torch.cuda.stream(stream):
-            for k in range(args.warmup + min(args.steps, 40)):
-                flush.fill_(float(k))
-                torch.cuda.synchronize()
-                t0 = time.perf_counter()
-                r = tr.track_host(hy, hz, hr, ev.counts, stream=stream)
-                M, H = r.sync()
-                bufs = host_bufs(bufs, M, H)
-                tpc_result_copy_to_host(r.handle, bufs)
-                t1 = time.perf_counter()
-                r.release()
-                if k >= args.warmup:
-                    times.append(t1 - t0)
-        serial_e2e = replica_throughput(reduce_max(sum(times), world, "cuda"), len(times), world)
-
-        # two in flight
-        nf = len(trackers)
-        pend, hb = [None] * nf, [None] * nf
-        moved = {"h2d": 0, "d2h": 0}
-
-        def retire(i, count):
-            r = pend[i]
-            M, H = r.sync()
-            hb[i] = host_bufs(hb[i], M, H)
-            tpc_result_copy_to_host(r.handle, hb[i])
-            r.release()
-            pend[i] = None
-            if count:
-                moved["d2h"] += M * (5 + 15 + 3 + 5) * 4 + H * 4 + 48
-
-        def pipelined(n, count):
-            for k in range(n):
-                i = k % nf
-                if pend[i] is not None:
-                    retire(i, count)
-                c_ = calls[k % len(calls)]
-                pend[i] = trackers[i].track_batch_host(c_["hy"], c_["hz"], c_["hr"], c_["counts"], B, stream=streams[i])
-                if count:
-                    moved["h2d"] += c_["n"] * 9
-            for i in range(nf):
-                if pend[i] is not None:
-                    retire(i, count)
-
-        pipelined(args.warmup * nf, False)
-        n_e2e = min(args.steps, max(40, 600 // B))
-        barrier()
-        t0 = time.perf_counter()
-        pipelined(n_e2e, True)
-        wall_e2e = time.perf_counter() - t0
-        e2e_v = replica_throughput(reduce_max(wall_e2e, world, "cuda"), n_e2e * B, world)
-        e2e = {"value": e2e_v, "unit": "events/s", "h2d_bytes_per_step": int(moved["h2d"] / n_e2e),
-               "d2h_bytes_per_step": int(moved["d2h"] / n_e2e), "steps": n_e2e, "events_per_step": B,
-               "path": "tpc_track_batch_host (pinned host input, %d events per call) + tpc_result_copy_to_host, "
-                       "wall clock, %d calls in flight on %d trackers" % (B, nf, nf),
-               "one_event_at_a_time": serial_e2e}
+    serving = None
+    if not args.no_serving and world == 1:
+        for t in trackers + trackers1:
+            t.close()
+        torch.cuda.synchronize()
+        torch.cuda.empty_cache()
+        serving = serving_leg(args, torch)
 
     if rank != 0:
         return 0
-    names = ["setup", "ingest", "neighbours", "evolution", "construction", "selection", "output", "global", "merge"]
-    mean_stage = stage_ms / n_serial
-    stages = {n: round(float(v), 4) for n, v in zip(names, mean_stage)}
     peak, peak_kind = measured_peaks()
-    cb = construct_bytes(stats)
-    con_ms = b_stage[4]
-    achieved = cb / (con_ms * 1e-3) / 1e9
+    stages_rf, total_rf, comp_rf = stage_roofline(b_units, b_stage, float(np.mean(b_ms)), peak)
+    con = stages_rf["construction"]
     traffic, winst, tnote = traffic_for_current_kernel()
+    seeded = B * n_mean / 20 > 2 * 152 * 6 * 128
     roof = {"kernel": "k_construct (A5 tracklet construction; %s)" % (
-                "pre-seeded, lanes meeting per row" if B * n_mean / 20 > 2 * 152 * 6 * 128 else "seeds walked per lane"),
-            "bound": "hbm", "achieved": achieved,
-            "peak": peak, "unit": "GB/s", "frac": achieved / peak, "peak_source": peak_kind + " (hbm_gbs)",
-            "traffic": traffic, "algorithmic_bytes": cb, "launch_ms": con_ms,
+                "pre-seeded, lanes meeting per row" if seeded else "seeds walked per lane"),
+            "bound": "hbm", "achieved": con["achieved_gbs"], "peak": peak, "unit": "GB/s", "frac": con["frac"],
+            "peak_source": peak_kind + " (hbm_gbs, burst copy)", "traffic": traffic,
+            "algorithmic_bytes": con["bytes"], "per_unit": con["per_unit"], "launch_ms": con["ms"],
+            "bytes_touched": construct_bytes_touched(
+                {"row_visits": b_units["V"], "candidates": b_units["K"], "tracklets": b_units["T"]}),
             "timed_in": "the step's call (%d events) one at a time, L2 flushed before each; construction stage "
-                        "(work order, seeds and the constructor)" % B, "units": stats}
+                        "(work order, seeds and the constructor), CUDA events on the call's stream" % B,
+            "units": b_units, "stages": stages_rf, "total": total_rf, "compulsory_io": comp_rf}
     if tnote:
         roof["traffic_note"] = tnote
     if winst:
-        # the kernel is L2-resident and issue-bound: its warp instructions (ncu) over the launch time
-        # against the issue rate of 152 SMs x 4 schedulers at the sampled SM clock
         sm_mhz = clk.get("sm_mhz") or 2070.0
         issue_peak = 152 * 4 * sm_mhz * 1e6
-        roof["issue"] = {"achieved": winst / (con_ms * 1e-3), "peak": issue_peak, "unit": "warp instructions/s",
-                         "frac": winst / (con_ms * 1e-3) / issue_peak, "warp_instructions": winst,
+        roof["issue"] = {"achieved": winst / (con["ms"] * 1e-3), "peak": issue_peak, "unit": "warp instructions/s",
+                         "frac": winst / (con["ms"] * 1e-3) / issue_peak, "warp_instructions": winst,
                          "peak_source": "152 SMs x 4 schedulers x sampled SM clock"}
     line = {"metric": METRIC, "value": value, "unit": "events/s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": 1e3 * total_s / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-            "config": {"workload": WORKLOAD, "resident_events": args.resident,
-                       "clusters_per_event": int(round(n_mean)), "events_per_call": B,
-                       "inflight_calls": args.inflight,
-                       "l2": "inputs larger than L2 (%d resident events, %.0f MB); no flush" % (
-                           args.resident, args.resident * n_mean * 9 / 1e6),
-                       "parallelism": "replicas" if world > 1 else "single GPU"},
+            "config": workload_config(len(pool), n_mean, world),
+            "launch": {"events_per_call": B, "inflight_calls": args.inflight, "calls_outstanding_per_tracker": QDEPTH,
+                       "warmup_calls": n_warm, "allocation": "workspace and %d result buffers per tracker "
+                                                             "preallocated (tpc_tracker_reserve_results)" % (QDEPTH + 1)},
             "clusters_per_s": value * n_mean, "tracks_per_event": int(np.mean(tracks)),
-            "one_event_per_call": one_per_call, "one_event_at_a_time": serial, "stages_ms": stages,
+            "one_event_per_call": one_per_call, "one_event_at_a_time": serial,
+            "stages_ms": {n: round(float(v), 4) for n, v in zip(STAGES, stage_ms / n_serial)},
             "one_call_at_a_time": {"ms_per_call": float(np.mean(b_ms)), "events_per_call": B,
-                                   "stages_ms": {n: round(float(v), 4) for n, v in zip(names, b_stage)},
-                                   "l2": "flushed before every call (512 MB write, untimed)"}, "global_tracking": global_line,
-            "global_tracking_and_merger": merge_line,
-            "gpu_launches": launches, "e2e": e2e, "roofline": roof, "clocks": clk,
+                                   "stages_ms": {n: round(float(v), 4) for n, v in zip(STAGES, b_stage)},
+                                   "l2": "flushed before every call (512 MB write, untimed)"},
+            "global_tracking": global_line, "global_tracking_and_merger": merge_line,
+            "gpu_launches": launches, "e2e": e2e, "serving": serving, "roofline": roof, "clocks": clk,
             "wall_s_timed_region": wall}
     if world == 1 and not args.no_cpu_baseline:
-        line["cpu_baseline"] = oracle_timing(ev)
+        line["cpu_baseline"] = oracle_timing(pool)
     print(json.dumps(line))
     return 0
+
+
+def e2e_leg(args, torch, pool, calls, trackers, streams, tr1, stream, flush, B, world):
+    from paper_1712_09407_gb300.tracker import tpc_result_copy_to_host
+
+    def host_bufs(bufs, M, H):
+        if bufs is None or bufs["par"].shape[0] < M or bufs["hits"].shape[0] < H:
+            bufs = dict(par=torch.empty((M + 1024, 5)).pin_memory(), cov=torch.empty((M + 1024, 15)).pin_memory(),
+                        x_ref=torch.empty(M + 1024).pin_memory(), alpha=torch.empty(M + 1024).pin_memory(),
+                        chi2=torch.empty(M + 1024).pin_memory(),
+                        **{n: torch.empty(M + 1024, dtype=torch.int32).pin_memory()
+                           for n in ("ndf", "nhits", "first", "sector", "event")},
+                        hits=torch.empty(H + 65536, dtype=torch.int32).pin_memory())
+        return bufs
+
+    # one at a time
+    bufs = None
+    times = []
+    with torch.cuda.stream(stream):
+        for k in range(args.warmup + min(max(args.steps, 10), 40)):
+            hy, hz, hr, counts, _ = pool[k % len(pool)]
+            flush.fill_(float(k))
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            r = tr1.track_host(hy, hz, hr, counts, stream=stream)
+            M, H = r.sync()
+            bufs = host_bufs(bufs, M, H)
+            tpc_result_copy_to_host(r.handle, bufs)
+            t1 = time.perf_counter()
+            r.release()
+            if k >= args.warmup:
+                times.append(t1 - t0)
+    serial_e2e = replica_throughput(reduce_max(sum(times), world, "cuda"), len(times), world)
+
+    # calls in flight, one per tracker
+    nf = len(trackers)
+    pend, hb = [None] * nf, [None] * nf
+    moved = {"h2d": 0, "d2h": 0}
+
+    def retire(i, count):
+        r = pend[i]
+        M, H = r.sync()
+        hb[i] = host_bufs(hb[i], M, H)
+        tpc_result_copy_to_host(r.handle, hb[i])
+        r.release()
+        pend[i] = None
+        if count:
+            moved["d2h"] += M * (5 + 15 + 3 + 5) * 4 + H * 4 + 48
+
+    def pipelined(n, count):
+        for k in range(n):
+            i = k % nf
+            if pend[i] is not None:
+                retire(i, count)
+            c_ = calls[k % len(calls)]
+            pend[i] = trackers[i].track_batch_host(c_["hy"], c_["hz"], c_["hr"], c_["counts"], B, stream=streams[i])
+            if count:
+                moved["h2d"] += c_["n"] * 9
+        for i in range(nf):
+            if pend[i] is not None:
+                retire(i, count)
+
+    pipelined(max(args.warmup, 2) * nf, False)
+    n_e2e = max(args.steps, 6 * nf)
+    torch.cuda.synchronize()
+    gc.disable()
+    t0 = time.perf_counter()
+    pipelined(n_e2e, True)
+    wall_e2e = time.perf_counter() - t0
+    gc.enable()
+    e2e_v = replica_throughput(reduce_max(wall_e2e, world, "cuda"), n_e2e * B, world)
+    return {"value": e2e_v, "unit": "events/s", "h2d_bytes_per_step": int(moved["h2d"] / n_e2e),
+            "d2h_bytes_per_step": int(moved["d2h"] / n_e2e), "steps": n_e2e, "events_per_step": B,
+            "path": "tpc_track_batch_host (pinned host input, %d events per call) + tpc_result_copy_to_host, "
+                    "wall clock, %d calls in flight on %d trackers" % (B, nf, nf),
+            "one_event_at_a_time": serial_e2e}
+
+
+def serving_leg(args, torch):
+    """Poisson arrivals of events of the batched workload (primaries log-uniform 500-16000, noise
+    5-20 %) through the native serving loop with continuous batching, and through the same loop
+    with one lane and one event per batch (the plain one-event-at-a-time path); a fixed 40 GB budget.
+    Latency runs from the scheduled arrival to the result in host memory."""
+    from paper_1712_09407_gb300 import eventgen
+    from paper_1712_09407_gb300.serving import (NativeServer, event_pool, latency_report, make_requests,
+                                                poisson_arrivals, run_stream_native)
+    pool = event_pool(args.serve_pool, cfg=3)
+    geo = eventgen.Geometry()
+    out = {"duration_s": args.serve_seconds, "pool_events": len(pool), "budget_gb": 40,
+           "workload": "events of the batched workload (primaries log-uniform 500-16000, noise 5-20 %%, seeds (1, i), "
+                       "i < %d), drawn with replacement" % len(pool),
+           "latency": "scheduled Poisson arrival to the event's result in host memory (copies included)"}
+    runs = [(200.0, "continuous_batching"), (200.0, "one_event_at_a_time"), (1000.0, "continuous_batching")]
+    for rate, mode in runs:
+        lanes, mb = (3, 16) if mode == "continuous_batching" else (1, 1)
+        srv = NativeServer(geo, lanes=lanes, hbm_budget=40 << 30, max_batch=mb, keep_results=False)
+        srv.warm(make_requests(pool, np.zeros(len(pool)), seed=99))
+        reqs = make_requests(pool, poisson_arrivals(rate, args.serve_seconds, seed=int(rate)), seed=int(rate))
+        wall = run_stream_native(srv, reqs)
+        rep = latency_report(reqs, wall)
+        rep.update(lanes=lanes, max_batch=mb)
+        out["%d_hz_%s" % (int(rate), mode)] = {k: (round(v, 4) if isinstance(v, float) else v) for k, v in rep.items()}
+        srv.close()
+        torch.cuda.synchronize()
+    return out
 
 
 def run_batch(args):

@@ -181,6 +181,23 @@ int tpc_tracker_set_tuning(tpc_tracker *tr, const tpc_tuning *t);
  * Errors: TPC_ERR_BUDGET, TPC_ERR_CUDA. */
 int tpc_tracker_reserve(tpc_tracker *tr, int64_t max_clusters, int max_events);
 
+/* Preallocate the device memory of `depth` results, each sized for the workspace reserved
+ * with tpc_tracker_reserve (its clusters and events), so that tracking calls allocate nothing
+ * at all: every call takes one of these result buffers and tpc_result_release gives it back.
+ * This is the preallocated output pool of a tracker that serves a stream of events (Section 2
+ * keeps the output buffers of each sector resident for the same reason; Section 6 reports a
+ * run that failed when a noisy sector exhausted device memory, which a fixed pool turns into a
+ * refusal instead).  Results held by the caller count against it: a call made while all
+ * `depth` results are held returns TPC_ERR_BUDGET and enqueues nothing.  A released result's
+ * buffers are reused by a later call only after the work enqueued on the released result's
+ * stream up to the release (e.g. the caller's copies of it) has finished.  A call larger than
+ * the reserved workspace grows the workspace and the buffer it takes (synchronously).
+ * depth = 0 returns to one allocation per call (buffers still held are freed at their release);
+ * a smaller depth than before frees the surplus.
+ * Errors: TPC_ERR_STATE (depth > 0 before any tpc_tracker_reserve), TPC_ERR_INVALID_ARG
+ * (depth < 0 or > 4096), TPC_ERR_BUDGET (the buffers exceed the HBM budget), TPC_ERR_CUDA. */
+int tpc_tracker_reserve_results(tpc_tracker *tr, int depth);
+
 /* Track one event (Section 1; all 36 sectors).  y, z, row: device arrays of n
  * clusters, owned by the caller, which must keep them valid until the stream has
  * passed this call's work.  counts: HOST array of n_sectors * n_rows counts in
@@ -271,12 +288,14 @@ typedef struct {
     int64_t global_found;          /* clusters found by the global-tracking prolongations (before claims) */
     int64_t graph_builds;          /* executable graphs the tracker instantiated up to this call (graph mode) */
     int64_t sector_tracks;         /* tracks before the merger (= tracks when it does not run) */
+    int64_t tracklet_hits;         /* A6 clusters of the tracklets that claim clusters */
 } tpc_call_stats;
 
 /* Host-side fault injection for failure tests; no GPU fault is involved.  what = 0: off;
- * 1: the neighbours finder's shared-memory staging of sector 0's middle row waits for 16
- * bytes that are never sent, so its bounded wait (1 s of device time) expires and the call reports
- * TPC_ERR_TIMEOUT with stage TPC_STAGE_NEIGHBOURS.  Returns TPC_ERR_INVALID_ARG otherwise. */
+ * 1: after the neighbours finder's shared-memory staging of sector 0's middle row has completed
+ * (no asynchronous copy is outstanding), its CTA also waits on a barrier that nothing completes,
+ * so that bounded wait (1 s of device time) expires and the call reports TPC_ERR_TIMEOUT with
+ * stage TPC_STAGE_NEIGHBOURS.  Returns TPC_ERR_INVALID_ARG otherwise. */
 int tpc_tracker_inject(tpc_tracker *tr, int what);
 
 /* Enable (1) or disable (0) per-stage event timing for the following calls. */

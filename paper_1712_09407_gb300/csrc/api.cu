@@ -25,7 +25,7 @@ struct NvtxRange {
 
 namespace {
 
-constexpr int kStaging = 4;             // ring of pinned staging buffers
+constexpr int kStaging = 8;             // ring of pinned staging buffers (calls of one tracker in flight)
 constexpr int kCountWords = CNT_COUNT + 4;
 
 struct Staging {
@@ -78,6 +78,11 @@ struct tpc_tracker {
     std::vector<int2> dims;
     std::vector<tpc_result *> free_results;   // released results, reused without new pinned allocations
     int64_t live_results = 0;                 // results handed out and not yet released
+    // result ring (tpc_tracker_reserve_results): result buffers allocated once, reused call after call
+    std::vector<tpc_result *> ring_free;      // ring results not held by the caller
+    int ring_depth = 0;                       // ring size asked for (0: every call allocates its result)
+    int ring_count = 0;                       // ring results in existence, free or held
+    size_t bytes_ring = 0;
     bool destroyed = false;                   // tpc_tracker_destroy was called; delete at the last release
     // last call
     int64_t last_units = 0, last_slots = 0, last_n = 0;
@@ -106,6 +111,12 @@ struct tpc_result {
     int64_t graph_builds = 0;            // the tracker's graph instantiations up to this call
     bool timed = false;
     cudaEvent_t stage_ev[10] = {};
+    // ring results only: device buffers sized once for cap_t tracks and cap_h hits; `reusable` is
+    // recorded on the call's stream at release, and the next call using the buffers waits for it
+    bool ring = false;
+    int64_t cap_t = 0, cap_h = 0;
+    cudaEvent_t reusable = nullptr;
+    bool reuse_pending = false;
 };
 
 bool tpc::tracker_info(const tpc_tracker *tr, TrackerInfo *out)
@@ -448,7 +459,7 @@ static int reserve(tpc_tracker *tr, int64_t n, int64_t events)
     Workspace keep = tr->w;
     size_t need = carve(tr, s, probe);
     tr->w = keep;
-    if (tr->budget && need + tr->bytes_results > tr->budget) return TPC_ERR_BUDGET;
+    if (tr->budget && need + tr->bytes_results + tr->bytes_ring > tr->budget) return TPC_ERR_BUDGET;
     if (tr->ws_base) {
         TPC_CUDA(cudaDeviceSynchronize());
         cudaFree(tr->ws_base);
@@ -503,6 +514,113 @@ static void carve_result(tpc_result *r, int64_t tcap, int64_t ncap)
     r->out.hcap = ncap;
 }
 
+// Result capacities of a call of n clusters: tracks <= tracklets <= n / min_chain (chains of
+// one-to-one links are disjoint) and the tracklet pool; hits <= n.
+static void result_caps(const tpc_tracker *tr, int64_t n, int64_t *tcap, int64_t *hcap)
+{
+    const int64_t tbound = n / (tr->params.min_chain > 0 ? tr->params.min_chain : 1) + 64;
+    *tcap = tr->w.tcap < tbound ? tr->w.tcap : tbound;
+    *hcap = n;
+}
+
+// (Re)size a ring result's device buffers for tcap tracks and hcap hits.  The result is free: its
+// last call has finished (released after tpc_result_sync_counts' wait) and its reusable event
+// is waited for before the old buffers go.
+static int ring_size(tpc_tracker *tr, tpc_result *r, int64_t tcap, int64_t hcap)
+{
+    const size_t bytes = result_bytes(tcap, hcap);
+    const size_t old = r->dev ? r->bytes : 0;
+    if (tr->budget && tr->bytes_ws + tr->bytes_results + tr->bytes_ring - old + bytes > tr->budget)
+        return TPC_ERR_BUDGET;
+    if (r->dev) {
+        if (r->reuse_pending) TPC_CUDA(cudaEventSynchronize(r->reusable));
+        r->reuse_pending = false;
+        cudaFree(r->dev);
+        r->dev = nullptr;
+        tr->bytes_ring -= old;
+        r->bytes = 0;
+    }
+    TPC_CUDA(cudaMalloc(&r->dev, bytes));
+    r->bytes = bytes;
+    r->cap_t = tcap;
+    r->cap_h = hcap;
+    tr->bytes_ring += bytes;
+    return TPC_OK;
+}
+
+// A new ring result with its pinned counters and events, buffers sized for the reserved workspace.
+static int ring_add(tpc_tracker *tr)
+{
+    tpc_result *r = new (std::nothrow) tpc_result();
+    if (!r) return TPC_ERR_CUDA;
+    r->ring = true;
+    r->tr = tr;
+    int64_t tcap, hcap;
+    result_caps(tr, tr->cap_n, &tcap, &hcap);
+    int s = TPC_OK;
+    if (cudaMallocHost((void **)&r->h_counts, kCountWords * sizeof(int32_t)) != cudaSuccess ||
+        cudaEventCreateWithFlags(&r->done, cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&r->reusable, cudaEventDisableTiming) != cudaSuccess)
+        s = TPC_ERR_CUDA;
+    for (auto &e : r->stage_ev)
+        if (s == TPC_OK && cudaEventCreate(&e) != cudaSuccess) s = TPC_ERR_CUDA;
+    if (s == TPC_OK) s = ring_size(tr, r, tcap, hcap);
+    if (s != TPC_OK) {
+        destroy_result(r);
+        return s;
+    }
+    tr->ring_free.push_back(r);
+    tr->ring_count++;
+    return TPC_OK;
+}
+
+// Free a ring result that no call uses any more.
+static void ring_drop(tpc_tracker *tr, tpc_result *r)
+{
+    if (r->reuse_pending) cudaEventSynchronize(r->reusable);
+    if (r->dev) cudaFree(r->dev);
+    r->dev = nullptr;
+    tr->bytes_ring -= r->bytes;
+    r->bytes = 0;
+    tr->ring_count--;
+    destroy_result(r);
+}
+
+extern "C" int tpc_tracker_reserve_results(tpc_tracker *tr, int depth)
+{
+    if (!tr || depth < 0 || depth > 4096) return TPC_ERR_INVALID_ARG;
+    std::lock_guard<std::mutex> g(tr->mu);
+    if (tr->destroyed) return TPC_ERR_STATE;
+    if (depth > 0 && tr->cap_n < 0) return TPC_ERR_STATE;     // sized from tpc_tracker_reserve's workspace
+    tr->ring_depth = depth;
+    while (tr->ring_count > depth && !tr->ring_free.empty()) {
+        tpc_result *r = tr->ring_free.back();
+        tr->ring_free.pop_back();
+        ring_drop(tr, r);
+    }
+    while (tr->ring_count < depth) {
+        const int s = ring_add(tr);
+        if (s != TPC_OK) return s;
+    }
+    return TPC_OK;
+}
+
+// A result handed back unused (the call failed before its work was enqueued).
+static void give_back(tpc_tracker *tr, tpc_result *r, cudaStream_t st)
+{
+    if (r->ring) {
+        tr->ring_free.push_back(r);
+        return;
+    }
+    if (r->dev) {
+        cudaFreeAsync(r->dev, st);
+        tr->bytes_results -= r->bytes;
+    }
+    r->dev = nullptr;
+    r->bytes = 0;
+    tr->free_results.push_back(r);
+}
+
 static int run(tpc_tracker *tr, const float *y, const float *z, const uint8_t *row, const int32_t *counts,
                int n_events, int64_t n_total, cudaStream_t st, tpc_result **out)
 {
@@ -519,45 +637,85 @@ static int run(tpc_tracker *tr, const float *y, const float *z, const uint8_t *r
     if (n_total > 0 && (!y || !z || !row)) return TPC_ERR_INVALID_ARG;
     int s = reserve(tr, n_total, n_events);
     if (s != TPC_OK) return s;
-    // result object: reuse a released one (its pinned count buffer and events) when possible
+    int64_t tcap, hcap;
+    result_caps(tr, n_total, &tcap, &hcap);
     tpc_result *res = nullptr;
-    if (!tr->free_results.empty()) {
-        res = tr->free_results.back();
-        tr->free_results.pop_back();
-        cudaEvent_t keep_done = res->done;
-        int32_t *keep_counts = res->h_counts;
-        cudaEvent_t keep_ev[10];
-        memcpy(keep_ev, res->stage_ev, sizeof keep_ev);
-        *res = tpc_result();
-        res->done = keep_done;
-        res->h_counts = keep_counts;
-        memcpy(res->stage_ev, keep_ev, sizeof keep_ev);
+    if (tr->ring_depth > 0) {
+        // preallocated result: the call allocates nothing; all ring results held -> not admitted
+        if (tr->ring_free.empty()) return TPC_ERR_BUDGET;
+        res = tr->ring_free.back();
+        tr->ring_free.pop_back();
+        if (res->cap_t < tcap || res->cap_h < hcap) {
+            // the workspace grew since the ring was sized: this buffer grows with it (synchronous)
+            int64_t rt, rh;
+            result_caps(tr, tr->cap_n, &rt, &rh);
+            s = ring_size(tr, res, rt > tcap ? rt : tcap, rh > hcap ? rh : hcap);
+            if (s != TPC_OK) {
+                tr->ring_free.push_back(res);
+                return s;
+            }
+        }
+        if (res->reuse_pending) {
+            s = cuda_fail(cudaStreamWaitEvent(st, res->reusable, 0));
+            if (s != TPC_OK) {
+                tr->ring_free.push_back(res);
+                return s;
+            }
+            res->reuse_pending = false;
+        }
+        res->synced = false;
+        res->status = TPC_OK;
+        res->n_tracks = res->n_hits = res->n_clusters = 0;
+        res->launches = 0;
+        res->timed = false;
+        res->stream = st;
+        carve_result(res, res->cap_t, res->cap_h);
     } else {
-        res = new (std::nothrow) tpc_result();
-        if (!res) return TPC_ERR_CUDA;
+        // result object: reuse a released one (its pinned count buffer and events) when possible
+        if (!tr->free_results.empty()) {
+            res = tr->free_results.back();
+            tr->free_results.pop_back();
+            cudaEvent_t keep_done = res->done;
+            int32_t *keep_counts = res->h_counts;
+            cudaEvent_t keep_ev[10];
+            memcpy(keep_ev, res->stage_ev, sizeof keep_ev);
+            *res = tpc_result();
+            res->done = keep_done;
+            res->h_counts = keep_counts;
+            memcpy(res->stage_ev, keep_ev, sizeof keep_ev);
+        } else {
+            res = new (std::nothrow) tpc_result();
+            if (!res) return TPC_ERR_CUDA;
+        }
+        res->tr = tr;
+        res->stream = st;
+        res->bytes = result_bytes(tcap, hcap);
+        if (tr->budget && tr->bytes_ws + tr->bytes_ring + tr->bytes_results + res->bytes > tr->budget) {
+            tr->free_results.push_back(res);
+            return TPC_ERR_BUDGET;
+        }
+        if (cudaMallocAsync(&res->dev, res->bytes, st) != cudaSuccess ||
+            (!res->h_counts && cudaMallocHost((void **)&res->h_counts, kCountWords * sizeof(int32_t)) != cudaSuccess) ||
+            (!res->done && cudaEventCreateWithFlags(&res->done, cudaEventDisableTiming) != cudaSuccess)) {
+            if (res->dev) cudaFreeAsync(res->dev, st);
+            res->dev = nullptr;
+            destroy_result(res);
+            return TPC_ERR_CUDA;
+        }
+        tr->bytes_results += res->bytes;
+        carve_result(res, tcap, hcap);
     }
-    res->tr = tr;
-    res->stream = st;
-    // tracks <= tracklets <= n / min_chain (chains of one-to-one links are disjoint)
-    const int64_t tbound = n_total / (tr->params.min_chain > 0 ? tr->params.min_chain : 1) + 64;
-    const int64_t tcap = tr->w.tcap < tbound ? tr->w.tcap : tbound;
-    const int64_t hcap = n_total;
-    res->bytes = result_bytes(tcap, hcap);
-    if (tr->budget && tr->bytes_ws + tr->bytes_results + res->bytes > tr->budget) {
-        tr->free_results.push_back(res);
-        return TPC_ERR_BUDGET;
-    }
-    if (cudaMallocAsync(&res->dev, res->bytes, st) != cudaSuccess ||
-        (!res->h_counts && cudaMallocHost((void **)&res->h_counts, kCountWords * sizeof(int32_t)) != cudaSuccess) ||
-        (!res->done && cudaEventCreateWithFlags(&res->done, cudaEventDisableTiming) != cudaSuccess)) {
-        if (res->dev) cudaFreeAsync(res->dev, st);
-        res->dev = nullptr;
-        destroy_result(res);
-        return TPC_ERR_CUDA;
-    }
-    tr->bytes_results += res->bytes;
-    carve_result(res, tcap, hcap);
-
+    // from here on a failure hands the result back
+    struct Guard {
+        tpc_tracker *tr;
+        tpc_result *r;
+        cudaStream_t st;
+        bool armed = true;
+        ~Guard()
+        {
+            if (armed) give_back(tr, r, st);
+        }
+    } guard{tr, res, st};
     // per row unit metadata
     tr->meta.resize(R);
     tr->dims.resize(R);
@@ -595,14 +753,7 @@ static int run(tpc_tracker *tr, const float *y, const float *z, const uint8_t *r
         const int bytes = rb(a.y, da.x * da.y) + rb(b.y, db.x * db.y);
         if (bytes > smem_need) smem_need = bytes;
     }
-    if (s_off + 64 > tr->w.pcap || c_off + 64 > tr->w.ccap) {
-        // cannot happen with ws_sizes' bounds; guard anyway
-        tr->bytes_results -= res->bytes;
-        cudaFreeAsync(res->dev, st);
-        res->dev = nullptr;
-        destroy_result(res);
-        return TPC_ERR_CAPACITY;
-    }
+    if (s_off + 64 > tr->w.pcap || c_off + 64 > tr->w.ccap) return TPC_ERR_CAPACITY;   // cannot happen with ws_sizes' bounds
     int smem = smem_need < neighbours_smem_limit() ? smem_need : neighbours_smem_limit();
 
     Staging &sg = tr->staging[tr->next_staging];
@@ -726,6 +877,7 @@ static int run(tpc_tracker *tr, const float *y, const float *z, const uint8_t *r
     TPC_CUDA(cudaEventRecord(res->done, st));
     TPC_CUDA(cudaEventRecord(tr->ws_done, st));
     tr->ws_used = true;
+    guard.armed = false;
     tr->live_results++;
     tr->last_units = R;
     tr->last_slots = s_off;
@@ -770,17 +922,24 @@ extern "C" int tpc_track_batch_host(tpc_tracker *tr, const float *y, const float
     if (tr->destroyed) return TPC_ERR_STATE;
     cudaStream_t st = (cudaStream_t)stream;
     if (n > tr->in_cap) {
+        // sized for the reserved workspace at least, so that calls up to that size never grow it again
+        const int64_t cap = n > tr->cap_n ? n : tr->cap_n;
         if (tr->in_base) {
             TPC_CUDA(cudaDeviceSynchronize());
             cudaFree(tr->in_base);
             tr->bytes_ws -= (size_t)tr->in_cap * 12;
             tr->in_base = nullptr;
+            tr->in_cap = 0;
         }
-        size_t need = (size_t)n * 12 + 1024;
-        if (tr->budget && tr->bytes_ws + tr->bytes_results + need > tr->budget) return TPC_ERR_BUDGET;
+        size_t need = (size_t)cap * 12 + 1024;
+        if (tr->budget && tr->bytes_ws + tr->bytes_ring + tr->bytes_results + need > tr->budget) {
+            if (cap == n) return TPC_ERR_BUDGET;
+            need = (size_t)n * 12 + 1024;            // the reserved size does not fit: this call's size
+            if (tr->bytes_ws + tr->bytes_ring + tr->bytes_results + need > tr->budget) return TPC_ERR_BUDGET;
+        }
         TPC_CUDA(cudaMalloc(&tr->in_base, need));
-        tr->in_cap = n;
-        tr->bytes_ws += (size_t)n * 12;
+        tr->in_cap = (int64_t)((need - 1024) / 12);
+        tr->bytes_ws += (size_t)tr->in_cap * 12;
     }
     float *dy = (float *)tr->in_base;
     float *dz = dy + tr->in_cap;
@@ -874,12 +1033,26 @@ static void free_tracker(tpc_tracker *tr);
 extern "C" void tpc_result_release(tpc_result *r)
 {
     if (!r) return;
-    if (r->dev) cudaFreeAsync(r->dev, r->stream);
-    r->dev = nullptr;
-    if (r->done) cudaEventSynchronize(r->done);
     tpc_tracker *tr = r->tr;
     bool last = false;
-    {
+    if (r->ring) {
+        // back to the ring: the next call that takes these buffers waits (on the device) for
+        // everything enqueued on this result's stream so far
+        if (r->done) cudaEventSynchronize(r->done);
+        std::lock_guard<std::mutex> g(tr->mu);
+        if (tr->destroyed || tr->ring_count > tr->ring_depth) {
+            ring_drop(tr, r);
+        } else {
+            r->reuse_pending = cudaEventRecord(r->reusable, r->stream) == cudaSuccess;
+            if (!r->reuse_pending) cudaStreamSynchronize(r->stream);
+            tr->ring_free.push_back(r);
+        }
+        tr->live_results--;
+        last = tr->destroyed && tr->live_results == 0;
+    } else {
+        if (r->dev) cudaFreeAsync(r->dev, r->stream);
+        r->dev = nullptr;
+        if (r->done) cudaEventSynchronize(r->done);
         std::lock_guard<std::mutex> g(tr->mu);
         tr->bytes_results -= r->bytes;
         r->bytes = 0;
@@ -892,6 +1065,8 @@ extern "C" void tpc_result_release(tpc_result *r)
 
 static void destroy_result(tpc_result *r)
 {
+    if (r->dev && r->ring) cudaFree(r->dev);
+    if (r->reusable) cudaEventDestroy(r->reusable);
     if (r->done) cudaEventDestroy(r->done);
     if (r->h_counts) cudaFreeHost(r->h_counts);
     for (auto &e : r->stage_ev)
@@ -917,6 +1092,11 @@ extern "C" void tpc_tracker_destroy(tpc_tracker *tr)
         tr->destroyed = true;
         if (tr->ws_base) cudaFree(tr->ws_base);
         if (tr->in_base) cudaFree(tr->in_base);
+        while (!tr->ring_free.empty()) {     // ring results the caller still holds go at their release
+            tpc_result *r = tr->ring_free.back();
+            tr->ring_free.pop_back();
+            ring_drop(tr, r);
+        }
         tr->ws_base = tr->in_base = nullptr;
         for (auto &st : tr->staging) {
             if (st.meta) cudaFreeHost(st.meta);
@@ -984,6 +1164,7 @@ extern "C" int tpc_result_stats(tpc_result *r, tpc_call_stats *st)
     st->global_found = r->h_counts[CNT_GPOOL];
     st->graph_builds = r->graph_builds;
     st->sector_tracks = r->tr->dc.merge ? r->h_counts[CNT_STRACKS] : r->h_counts[CNT_TRACKS];
+    st->tracklet_hits = r->h_counts[CNT_TLHITS];
     return TPC_OK;
 }
 

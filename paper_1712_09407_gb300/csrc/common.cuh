@@ -34,7 +34,8 @@ enum {
     CNT_STRACKS = 9,    // merger: sector tracks (CNT_TRACKS then counts the merged tracks)
     CNT_SHITS = 10,     // merger: clusters of the sector tracks
     CNT_GEDGE = 11,     // global tracking: prolongations past the edge test
-    CNT_COUNT = 12
+    CNT_TLHITS = 12,    // A6: clusters of the tracklets that claim (statistics)
+    CNT_COUNT = 13
 };
 
 // Constants of one tracker, passed by value to every kernel (kernel parameter space).
@@ -59,7 +60,7 @@ struct DevConst {
     int max_miss;
     int min_chain;
     int min_clusters;
-    int inject;         // host-side test hook (0 = off): 1 makes one staging wait of the neighbours finder expire
+    int inject;         // host-side test hook (0 = off): 1 makes one bounded wait of the neighbours finder expire
     int global;         // global tracking on (Section 5)
     float c20, s20;     // cos, sin of the 20 degree sector pitch
     int merge;          // track merger with refit

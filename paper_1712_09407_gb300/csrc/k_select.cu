@@ -166,9 +166,11 @@ __global__ void __launch_bounds__(256) k_count(const DevConst c, const Workspace
     const int T = n_tracklets(w);
     const int lane = threadIdx.x & 31;
     const int nwarps = (gridDim.x * blockDim.x) >> 5;
+    int nsum = 0;       // clusters of the claiming tracklets (statistics), one atomic per warp
     for (int t = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; t < T; t += nwarps) {
         const unsigned long long key = w.tl_key[t];
         const int n = key ? w.tl_n[t] : 0;
+        nsum += n;
         const int32_t *h = w.tl_hits + (int64_t)t * c.nr;
         int owned = 0, inner_i = -1;
         for (int i0 = 0; i0 < n; i0 += 32) {
@@ -190,6 +192,7 @@ __global__ void __launch_bounds__(256) k_count(const DevConst c, const Workspace
             w.tl_inner[t] = inner;
         }
     }
+    if (lane == 0 && nsum) atomicAdd(&w.counters[CNT_TLHITS], nsum);
 }
 
 int launch_select(const DevConst &c, const Workspace &w, int64_t n_input, const LaunchCfg &lc, cudaStream_t s)

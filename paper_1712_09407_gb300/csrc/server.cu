@@ -308,6 +308,7 @@ extern "C" int tpc_server_create(const tpc_geometry *g, float bz, const tpc_para
         }
         st = tpc_tracker_create(g, bz, params, per_lane ? per_lane - in_bytes : 0, &L.tr);
         if (st == TPC_OK) st = tpc_tracker_reserve(L.tr, cfg->lane_clusters, cfg->max_batch);
+        if (st == TPC_OK) st = tpc_tracker_reserve_results(L.tr, 1);     // a lane holds one result at a time
         if (st != TPC_OK) break;
         if (cudaStreamCreateWithFlags(&L.st, cudaStreamNonBlocking) != cudaSuccess ||
             cudaEventCreateWithFlags(&L.copied, cudaEventDisableTiming) != cudaSuccess ||

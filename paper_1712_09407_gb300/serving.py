@@ -32,8 +32,9 @@ from .tracker import (Tracker, TrackerError, server_result_arrays, tpc_result_co
                       tpc_server_destroy, tpc_server_get, tpc_server_now_ns, tpc_server_poll, tpc_server_release,
                       tpc_server_submit)
 
-# device bytes per reserved cluster: workspace (about 230 B), result (about 32 B), input (9 B)
-BYTES_PER_CLUSTER = 280
+# device bytes per reserved cluster: workspace (about 246 B), the lane's preallocated result
+# (about 32 B), input (9 B), with a margin
+BYTES_PER_CLUSTER = 300
 
 
 @dataclasses.dataclass
@@ -349,8 +350,9 @@ def _gen(args):
     return ev.y, ev.z, ev.row, ev.counts
 
 
-def event_pool(n_events, cfg=3, workers=8, first_event=0):
-    """Pre-generated events (drawn with replacement during a run), pinned in host memory."""
+def event_pool(n_events, cfg=3, workers=8, first_event=0, pin=True):
+    """Pre-generated events (drawn with replacement during a run): torch tensors, pinned in host
+    memory unless ``pin`` is False (no CUDA needed then)."""
     import concurrent.futures as cf
     import multiprocessing as mp
     import torch
@@ -358,8 +360,10 @@ def event_pool(n_events, cfg=3, workers=8, first_event=0):
         evs = list(ex.map(_gen, [(cfg, first_event + i) for i in range(n_events)]))
     pool = []
     for y, z, row, counts in evs:
-        pool.append((torch.from_numpy(y).pin_memory(), torch.from_numpy(z).pin_memory(),
-                     torch.from_numpy(row).pin_memory(), counts, int(y.shape[0])))
+        t = [torch.from_numpy(a) for a in (y, z, row)]
+        if pin:
+            t = [a.pin_memory() for a in t]
+        pool.append((t[0], t[1], t[2], counts, int(y.shape[0])))
     return pool
 
 

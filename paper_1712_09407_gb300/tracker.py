@@ -67,7 +67,8 @@ class tpc_debug_view(ctypes.Structure):
 class tpc_call_stats(ctypes.Structure):
     _fields_ = [("ms", c_float * 10), ("kernel_launches", c_int), ("clusters", c_int64), ("tracklets", c_int64),
                 ("row_visits", c_int64), ("candidates", c_int64), ("tracks", c_int64), ("hits", c_int64),
-                ("global_found", c_int64), ("graph_builds", c_int64), ("sector_tracks", c_int64)]
+                ("global_found", c_int64), ("graph_builds", c_int64), ("sector_tracks", c_int64),
+                ("tracklet_hits", c_int64)]
 
 
 class tpc_server_config(ctypes.Structure):
@@ -86,6 +87,7 @@ EXPORTS = {
     "tpc_tracker_create": (c_int, [P(tpc_geometry), c_float, P(tpc_params), ctypes.c_size_t, P(c_void_p)]),
     "tpc_tracker_set_tuning": (c_int, [c_void_p, P(tpc_tuning)]),
     "tpc_tracker_reserve": (c_int, [c_void_p, c_int64, c_int]),
+    "tpc_tracker_reserve_results": (c_int, [c_void_p, c_int]),
     "tpc_track_event": (c_int, [c_void_p, c_void_p, c_void_p, c_void_p, c_void_p, c_int64, c_void_p, P(c_void_p)]),
     "tpc_track_batch": (c_int, [c_void_p, c_void_p, c_void_p, c_void_p, c_void_p, c_int, c_int64, c_void_p,
                                 P(c_void_p)]),
@@ -185,6 +187,10 @@ def tpc_tracker_set_tuning(tr, tuning):
 
 def tpc_tracker_reserve(tr, max_clusters, max_events=1):
     _check(lib().tpc_tracker_reserve(tr, int(max_clusters), int(max_events)), "tpc_tracker_reserve")
+
+
+def tpc_tracker_reserve_results(tr, depth):
+    _check(lib().tpc_tracker_reserve_results(tr, int(depth)), "tpc_tracker_reserve_results")
 
 
 def _ptr(t):
@@ -352,7 +358,7 @@ def tpc_result_stats(res) -> dict:
     return dict(ms=list(st.ms)[:9], kernel_launches=st.kernel_launches, clusters=st.clusters,
                 tracklets=st.tracklets, row_visits=st.row_visits, candidates=st.candidates, tracks=st.tracks,
                 hits=st.hits, global_found=st.global_found, graph_builds=st.graph_builds,
-                sector_tracks=st.sector_tracks)
+                sector_tracks=st.sector_tracks, tracklet_hits=st.tracklet_hits)
 
 
 def tpc_find_links_noalloc(tr, y, z, row, counts, up, dn, status=None, stream=None, n=None):
@@ -489,8 +495,12 @@ class Tracker:
             tuning = t
         tpc_tracker_set_tuning(self.handle, tuning)
 
-    def reserve(self, max_clusters, max_events=1):
+    def reserve(self, max_clusters, max_events=1, results=None):
+        """Size the workspace; with ``results`` also preallocate that many result buffers, after
+        which calls allocate no device memory (a call while all are held raises TPC_ERR_BUDGET)."""
         tpc_tracker_reserve(self.handle, max_clusters, max_events)
+        if results is not None:
+            tpc_tracker_reserve_results(self.handle, results)
 
     def track(self, y, z, row, counts, stream=None) -> Result:
         return Result(tpc_track_event(self.handle, y, z, row, counts, stream), self)
