@@ -85,6 +85,7 @@ extern "C" int tpc_find_links_noalloc(tpc_tracker *tr, const float *y, const flo
     cudaStream_t st = (cudaStream_t)stream;
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 256) return TPC_ERR_CUDA;
+    cudaGetLastError();     // a launch error left over from earlier work of this thread is not this call's
 
     std::lock_guard<std::mutex> g(g_mu);
     if (!g_addr[dev]) {
@@ -156,13 +157,17 @@ extern "C" int tpc_find_links_noalloc(tpc_tracker *tr, const float *y, const flo
     lc.neighbours_block = ti.neighbours_block;
     lc.stage_rows = ti.stage_rows;
     lc.neighbours_smem_max = smem;
+    // every launch is checked on its own
     launch_ingest(*ti.dc, w, y, z, row, R, st);
+    if (cudaGetLastError() != cudaSuccess) return TPC_ERR_CUDA;
     launch_neighbours(*ti.dc, w, R, smem, lc, st);
+    if (cudaGetLastError() != cudaSuccess) return TPC_ERR_CUDA;
     if (R > 0) {
         int64_t grid = R < 65535 * 4 ? R : 65535 * 4;
         k_evolve_links<<<(unsigned)grid, 128, 0, st>>>(w, R, up, dn);
+        if (cudaGetLastError() != cudaSuccess) return TPC_ERR_CUDA;
     }
     if (status && cudaMemcpyAsync(status, w.err, 4 * sizeof(int32_t), cudaMemcpyDeviceToDevice, st) != cudaSuccess)
         return TPC_ERR_CUDA;
-    return cudaGetLastError() == cudaSuccess ? TPC_OK : TPC_ERR_CUDA;
+    return TPC_OK;
 }
