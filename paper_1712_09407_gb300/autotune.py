@@ -42,8 +42,22 @@ def time_stages(tracker: Tracker, y, z, row, counts, tuning: dict, repeats: int 
     return np.median(np.array(ms), axis=0)
 
 
-def tune(tracker: Tracker, y, z, row, counts, repeats: int = 3, stream=None, log=None) -> dict:
-    """Coordinate search over the tuning space; returns the best tuning as a dict."""
+# The search, in order: (field, candidates, stages whose time decides).
+SPACE = [
+    ("bin_occupancy", [0.5, 1.0, 1.5, 2.0, 3.0, 4.0], ["ingest", "neighbours", "construction"]),
+    ("stage_rows", [0, 1], ["neighbours"]),
+    ("neighbours_block", [64, 128, 256], ["neighbours"]),
+    ("construct_block", [64, 96, 128], ["construction"]),
+    ("construct_ctas_per_sm", [0, 4, 6, 8, 10, 12], ["construction"]),
+    ("seed_kernel", [0, 1], ["construction"]),
+    ("use_graph", [0, 1], STAGES),
+]
+
+
+def tune(tracker: Tracker, y, z, row, counts, repeats: int = 3, stream=None, log=None, space=None) -> dict:
+    """Coordinate search over the tuning space (``space``: a list like SPACE, default SPACE); each
+    field in turn takes its candidate with the least time of the stages it affects, the others
+    held at their best so far.  Returns the best tuning as a dict and sets it on the tracker."""
     best = _as_dict(tpc_tuning_default())
 
     def cost(t, stages):
@@ -61,13 +75,8 @@ def tune(tracker: Tracker, y, z, row, counts, repeats: int = 3, stream=None, log
             scores.append((cost(t, stages), v))
         best[field] = min(scores)[1]
 
-    search("bin_occupancy", [0.5, 1.0, 1.5, 2.0, 3.0, 4.0], ["ingest", "neighbours", "construction"])
-    search("stage_rows", [0, 1], ["neighbours"])
-    search("neighbours_block", [64, 128, 256], ["neighbours"])
-    search("construct_block", [64, 96, 128], ["construction"])
-    search("construct_ctas_per_sm", [0, 4, 6, 8, 10, 12], ["construction"])
-    search("seed_kernel", [0, 1], ["construction"])
-    search("use_graph", [0, 1], STAGES)
+    for field, values, stages in (SPACE if space is None else space):
+        search(field, values, stages)
     tracker.set_tuning(best)
     return best
 
