@@ -98,27 +98,34 @@ def replica_event(rank: int) -> int:
 # clocks during the timed region
 # ------------------------------------------------------------------------------------------------
 class ClockSampler:
-    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
-              "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
-              "clocks_event_reasons.sw_power_cap")
+    """nvidia-smi samples of the SM clock and throttle reasons every 50 ms, started well before
+    the timed region (so that its start-up does not coincide with it); stop() summarises the
+    samples taken inside the marked window."""
+    FIELDS = ("timestamp,index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
 
     def __init__(self, index):
         self.index = index
         self.proc = None
         self.path = None
+        self.windows = []
 
     def start(self):
         fd, self.path = tempfile.mkstemp(suffix=".csv")
         os.close(fd)
         try:
             self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.FIELDS,
-                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                          "--format=csv,noheader,nounits", "-lms", "50"],
                                          stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
         except OSError:
             self.proc = None
-        time.sleep(0.3)
 
-    def stop(self):
+    def mark(self, t0, t1):
+        """A timed window in time.time() seconds."""
+        self.windows.append((t0, t1))
+
+    def stop(self, window=-1):
         if self.proc is None:
             return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
         self.proc.terminate()
@@ -126,26 +133,36 @@ class ClockSampler:
             self.proc.wait(timeout=5)
         except subprocess.TimeoutExpired:
             self.proc.kill()
+        import datetime
         rows = []
         for line in open(self.path):
             parts = [p.strip() for p in line.split(",")]
-            if len(parts) >= 9:
-                rows.append(parts)
+            if len(parts) >= 10:
+                try:
+                    ts = datetime.datetime.strptime(parts[0], "%Y/%m/%d %H:%M:%S.%f").timestamp()
+                except ValueError:
+                    continue
+                rows.append([ts] + parts[1:])
         os.unlink(self.path)
         if not rows:
             return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        t0, t1 = self.windows[window] if self.windows else (rows[0][0], rows[-1][0])
+        inside = [r for r in rows if t0 - 0.05 <= r[0] <= t1 + 0.05]
+        if not inside:                                     # a window shorter than the sampling period
+            inside = sorted(rows, key=lambda r: abs(r[0] - 0.5 * (t0 + t1)))[:2]
 
         def num(x):
             try:
                 return float(x)
             except ValueError:
                 return None
-        sm = [num(r[1]) for r in rows if num(r[1])]
-        mx = max(num(r[2]) or 0 for r in rows)
+        sm = [num(r[2]) for r in inside if num(r[2])]
+        mx = max(num(r[3]) or 0 for r in rows)
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        reasons = sorted({names[i] for r in rows for i in range(4) if r[5 + i].lower().startswith("active")})
+        reasons = sorted({names[i] for r in inside for i in range(4) if r[6 + i].lower().startswith("active")})
         return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": mx, "reasons": reasons,
-                "samples": len(rows), "power_w_max": max(num(r[3]) or 0 for r in rows)}
+                "samples": len(inside), "power_w_max": max(num(r[4]) or 0 for r in inside),
+                "sampling": "every 50 ms; samples within the timed region"}
 
 
 # ------------------------------------------------------------------------------------------------
@@ -340,6 +357,7 @@ def run_reference(args):
 # our arm
 # ------------------------------------------------------------------------------------------------
 QDEPTH = 6     # calls each tracker has outstanding in the streamed legs (its result ring holds one more)
+PREROLL_CYCLES = 10_000_000   # about 5 ms at 2 GHz
 STAGES = ["setup", "ingest", "neighbours", "evolution", "construction", "selection", "output", "global", "merge"]
 
 
@@ -365,8 +383,14 @@ class Streamer:
         start = ends = None
         if timed:
             self.barrier()
+            self.t_host = time.time()
             start = torch.cuda.Event(enable_timing=True)
             ends = [torch.cuda.Event(enable_timing=True) for _ in self.streams]
+            # untimed pre-roll: the device spins for about 5 ms before the start event, so that the
+            # first calls are already queued when the region starts (the host's enqueue time of the
+            # first calls is not device time; the end-to-end leg measures the host path)
+            with torch.cuda.stream(self.streams[0]):
+                torch.cuda._sleep(PREROLL_CYCLES)
             start.record(self.streams[0])
             for s_ in self.streams[1:]:
                 s_.wait_event(start)
@@ -392,6 +416,8 @@ class Streamer:
         while pend:
             retire(pend.popleft())
         total_s = max(start.elapsed_time(e) for e in ends) / 1e3 if timed else None
+        if timed:
+            self.t_host_end = time.time()
         if gc_was:
             gc.enable()
         return total_s, launches, tracks
@@ -412,6 +438,8 @@ def run_ours(args):
 
     # Resident inputs: `resident` different central-like events (together more than the 129 MB L2),
     # copied to HBM before any timing; rank r tracks its own events (replicas)
+    clocks = ClockSampler(local)
+    clocks.start()                   # long before the timed region; only its samples are kept
     pool = resident_events(args.resident, replica_event(rank) * args.resident, pin=True)
     geo = eventgen.Geometry()
     dev = [(p[0].cuda(), p[1].cuda(), p[2].cuda(), p[3], p[4]) for p in pool]
@@ -460,11 +488,10 @@ def run_ours(args):
 
     # ---- timed region (the value): a stream of calls of B central-like events each, `inflight` calls
     # on the device at once (one tracker and stream each); per-call stage timing stays off here
-    clocks = ClockSampler(local)
-    clocks.start()
     t_wall = time.perf_counter()
     total_s, launches, tracks = sb.run(args.steps, call_b, timed=True)
     wall = time.perf_counter() - t_wall
+    clocks.mark(sb.t_host, sb.t_host_end)
     clk = clocks.stop()
     total_s = reduce_max(total_s, world, "cuda")
     value = replica_throughput(total_s, args.steps * B, world)
@@ -588,7 +615,7 @@ def run_ours(args):
     stages_rf, total_rf, comp_rf = stage_roofline(b_units, b_stage, float(np.mean(b_ms)), peak)
     con = stages_rf["construction"]
     traffic, winst, tnote = traffic_for_current_kernel()
-    seeded = B * n_mean / 20 > 2 * 152 * 6 * 128
+    seeded = B * n_mean / 20 > 2 * 152 * 5 * 128
     roof = {"kernel": "k_construct (A5 tracklet construction; %s)" % (
                 "pre-seeded, lanes meeting per row" if seeded else "seeds walked per lane"),
             "bound": "hbm", "achieved": con["achieved_gbs"], "peak": peak, "unit": "GB/s", "frac": con["frac"],

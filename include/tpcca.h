@@ -176,8 +176,9 @@ int tpc_tracker_create(const tpc_geometry *geometry, float bz_tesla, const tpc_p
 /* Replace the launch choices (host struct, copied).  Results are unchanged. */
 int tpc_tracker_set_tuning(tpc_tracker *tr, const tpc_tuning *t);
 
-/* Pre-size the device workspace for batches of up to max_clusters clusters and
- * max_events events, so that later calls of that size allocate nothing.
+/* Pre-size the device workspace and the pinned host staging of the per-row metadata for
+ * batches of up to max_clusters clusters and max_events events, so that later calls of that
+ * size allocate nothing but their result (see tpc_tracker_reserve_results for those).
  * Errors: TPC_ERR_BUDGET, TPC_ERR_CUDA. */
 int tpc_tracker_reserve(tpc_tracker *tr, int64_t max_clusters, int max_events);
 

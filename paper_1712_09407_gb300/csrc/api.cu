@@ -477,10 +477,36 @@ static int reserve(tpc_tracker *tr, int64_t n, int64_t events)
     return TPC_OK;
 }
 
+// Pinned host staging of the per-unit metadata for calls of up to R row units: every buffer of
+// the ring, so that no call allocates pinned memory later.
+static int reserve_staging(tpc_tracker *tr, int64_t R)
+{
+    for (auto &sg : tr->staging) {
+        if (sg.cap >= R) continue;
+        if (sg.pending) {
+            TPC_CUDA(cudaEventSynchronize(sg.consumed));
+            sg.pending = false;
+        }
+        if (sg.meta) cudaFreeHost(sg.meta);
+        if (sg.dims) cudaFreeHost(sg.dims);
+        sg.meta = nullptr;
+        sg.dims = nullptr;
+        sg.cap = 0;
+        const int64_t cap = R < 1 ? 1 : R;
+        TPC_CUDA(cudaMallocHost((void **)&sg.meta, cap * sizeof(int4)));
+        TPC_CUDA(cudaMallocHost((void **)&sg.dims, cap * sizeof(int2)));
+        sg.cap = cap;
+    }
+    return TPC_OK;
+}
+
 extern "C" int tpc_tracker_reserve(tpc_tracker *tr, int64_t max_clusters, int max_events)
 {
     if (!tr || max_clusters < 0 || max_events < 1) return TPC_ERR_INVALID_ARG;
-    return reserve(tr, max_clusters, max_events);
+    std::lock_guard<std::mutex> g(tr->mu);
+    const int s = reserve(tr, max_clusters, max_events);
+    if (s != TPC_OK) return s;
+    return reserve_staging(tr, (int64_t)max_events * tr->n_sectors * tr->n_rows);
 }
 
 static size_t result_bytes(int64_t tcap, int64_t ncap)

@@ -128,6 +128,8 @@ __global__ void __launch_bounds__(256) k_seed(const DevConst c, const Workspace 
     }
 }
 
+constexpr int kSearchBatch = 4;   // candidates whose loads a row search issues together
+
 // Row search and Kalman update of one lane's row visit: the best cluster within the chi2 gate
 // updates the state (and, on the inward pass, is recorded as a hit), otherwise the row is a miss.
 // Returns true when the pass stops (max_miss misses in a row).
@@ -138,9 +140,8 @@ __device__ __forceinline__ bool search_and_update(const DevConst &c, const Works
     visits++;
     const Gain g = residual_cov_inv(pr, c);
     float chi2 = 0.0f;
-    float2 q_unused;      // reloaded below instead: keeping it live costs spills at 80 registers
-    const int bl = search_cells(c, w.yz + rg.x, w.orig + rg.x, w.cell + rg.y, gr, rg.z, rg.w, pr, g, chi2, q_unused,
-                                cands);
+    const int bl = search_cells_mlp<kSearchBatch>(c, w.yz + rg.x, w.orig + rg.x, w.cell + rg.y, gr, rg.z, rg.w, pr, g,
+                                                  chi2, cands);
     const int b = bl < 0 ? -1 : rg.x + bl;
     if (b >= 0 && chi2 <= c.chi2max) {
         const float2 q = __ldg(w.yz + b);
@@ -191,7 +192,8 @@ __device__ __forceinline__ void next_row(const DevConst &c, const Workspace &w, 
     }
 }
 
-// 128 threads and 6 resident CTAs per SM: 80 registers without spills (measured fastest).
+// 128 threads and 5 resident CTAs per SM: 96 registers, no spills; with the batched row search
+// this is faster than 6 CTAs at 80 registers (spills) or 4 at up to 128 (measured).
 // GLOBAL: also store the outward pass's final state (the outer end for global tracking); a
 // separate instance so that the plain tracker keeps its register allocation.
 // PRESEED selects between two shapes of the same loop (same rows, same arithmetic, same results):
@@ -203,7 +205,7 @@ __device__ __forceinline__ void next_row(const DevConst &c, const Workspace &w, 
 //   transport search together instead of in separate passes of the visit.  Throughput-bound, so
 //   fewer issued instructions win over waiting.
 template <bool GLOBAL, bool PRESEED>
-__global__ void __launch_bounds__(128, 6)
+__global__ void __launch_bounds__(128, 5)
 k_construct(const DevConst c, const Workspace w)
 {
     const int T = n_tracklets(w);
@@ -324,9 +326,9 @@ int launch_construct(const DevConst &c, const Workspace &w, const LaunchCfg &lc,
         per_sm = occ > 0 ? occ : 1;
     }
     // seed kernel (and the pre-seeded constructor) when the call is expected to give each resident
-    // lane at least two tracklets (about one start hit per 20 clusters in central-like events; 6
+    // lane at least two tracklets (about one start hit per 20 clusters in central-like events; 5
     // resident CTAs per SM): two central-like events per call and more
-    const int64_t lanes = (int64_t)lc.num_sms * 6 * lc.construct_block;
+    const int64_t lanes = (int64_t)lc.num_sms * 5 * lc.construct_block;
     const bool preseed = lc.seed_kernel > 0 || (lc.seed_kernel < 0 && lc.n_clusters / 20 > 2 * lanes);
     // groups of order_group slots, as many as the histogram's kOrderCursors buckets hold
     const int kb = order_kb(c.nr), max_groups = kOrderCursors / kb;

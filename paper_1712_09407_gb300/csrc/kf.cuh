@@ -285,6 +285,69 @@ __device__ __forceinline__ int search_cells(const DevConst &c, const float2 *yz,
     return b.best;
 }
 
+// The same row search for rows in global memory, arranged for memory-level parallelism: the slot
+// ranges of the window's first three cell rows are loaded together, then the candidates are
+// loaded CB at a time before any of them is tested, so that a visit waits for about two or three
+// L2 round trips instead of one per candidate and per cell row.  Cell rows beyond the third
+// (windows wider than three cells in z, rare) follow one at a time.  The best cluster is the
+// lexicographic minimum of (chi2, input index) over the same candidates, whatever order they are
+// offered in, so the result is identical to search_cells.  Statistics: ncand counts the clusters
+// of every enumerated cell, as there.
+template <int CB>
+__device__ __forceinline__ int search_cells_mlp(const DevConst &c, const float2 *__restrict__ yz,
+                                                const int32_t *__restrict__ orig, const int32_t *__restrict__ cell,
+                                                const float4 gr, int ny, int nz, const KF &pr, const Gain &g,
+                                                float &chi2_out, int &ncand)
+{
+    const float wy = c.nsig * sqrtf(pr.c00 + c.sy2);
+    const float wz = c.nsig * sqrtf(pr.c11 + c.sz2);
+    const float y = pr.p0, z = pr.p1;
+    const int iy0 = cell1(y - wy - kBinSlack, gr.x, gr.z, ny);
+    const int iy1 = cell1(y + wy + kBinSlack, gr.x, gr.z, ny);
+    const int iz0 = cell1(z - wz - kBinSlack, gr.y, gr.w, nz);
+    const int iz1 = cell1(z + wz + kBinSlack, gr.y, gr.w, nz);
+    const int32_t *c0 = cell + iz0 * ny;
+    const int a0 = __ldg(c0 + iy0), e0 = __ldg(c0 + iy1 + 1);
+    int a1 = 0, e1 = 0, a2 = 0, e2 = 0;
+    if (iz1 > iz0) {
+        a1 = __ldg(c0 + ny + iy0);
+        e1 = __ldg(c0 + ny + iy1 + 1);
+    }
+    if (iz1 > iz0 + 1) {
+        a2 = __ldg(c0 + 2 * ny + iy0);
+        e2 = __ldg(c0 + 2 * ny + iy1 + 1);
+    }
+    const int n0 = e0 - a0, n01 = n0 + (e1 - a1), n = n01 + (e2 - a2);
+    ncand += n;
+    BestCand b;
+    for (int i0 = 0; i0 < n; i0 += CB) {
+        int sl[CB];
+        float2 q[CB];
+#pragma unroll
+        for (int k = 0; k < CB; k++) {
+            const int i = i0 + k;
+            sl[k] = i < n0 ? a0 + i : (i < n01 ? a1 + (i - n0) : a2 + (i - n01));
+        }
+#pragma unroll
+        for (int k = 0; k < CB; k++) q[k] = i0 + k < n ? __ldg(yz + sl[k]) : make_float2(0.0f, 0.0f);
+#pragma unroll
+        for (int k = 0; k < CB; k++) {
+            if (i0 + k < n && fabsf(q[k].x - y) <= wy && fabsf(q[k].y - z) <= wz)
+                b.offer(sl[k], q[k], chi2_of(g, q[k].x - y, q[k].y - z), orig);
+        }
+    }
+    for (int iz = iz0 + 3; iz <= iz1; iz++) {
+        const int a = __ldg(cell + iz * ny + iy0), e = __ldg(cell + iz * ny + iy1 + 1);
+        ncand += e - a;
+        for (int k = a; k < e; k++) {
+            const float2 q = __ldg(yz + k);
+            if (fabsf(q.x - y) <= wy && fabsf(q.y - z) <= wz) b.offer(k, q, chi2_of(g, q.x - y, q.y - z), orig);
+        }
+    }
+    chi2_out = b.bc;
+    return b.best;
+}
+
 // Writes a finished tracklet: state at its innermost fitted cluster, chi2, weight and the 64-bit
 // claim key used by the selection (Section 3.1: w = n (alpha - chi2/beta), chi2 read per degree
 // of freedom; ties to the lower input index of the start cluster).
