@@ -114,7 +114,10 @@ typedef struct {
     int construct_ctas_per_sm; /* persistent CTAs per SM of the work-queue constructor (0 = occupancy limit) */
     int construct_mode;        /* 0: one lane per tracklet from a work queue; 1: per-sector row sweep with rows
                                   staged in shared memory.  Same visits, same arithmetic, same results. */
-    int stage_rows;            /* 1: stage rows k-1, k+1 into shared memory with bulk copies */
+    int stage_rows;            /* form of the neighbours finder: 0 one thread per cluster, rows k-1, k+1 read from
+                                  global memory; 1 the same with the rows staged into shared memory by bulk
+                                  copies (default); 2 warp-cooperative search on the staged rows (candidates
+                                  and pairs of 32 clusters spread over the lanes).  Same links in every form. */
     int tracklet_capacity;     /* 0: n/4 + 64 per call; > 0: store at most this many tracklets (a capacity
                                   knob: more start hits make the call fail with TPC_ERR_CAPACITY) */
     int use_graph;             /* 1: every call's copies, clears and kernels are captured into a CUDA graph
@@ -293,7 +296,8 @@ typedef struct {
 } tpc_call_stats;
 
 /* Host-side fault injection for failure tests; no GPU fault is involved.  what = 0: off;
- * 1: after the neighbours finder's shared-memory staging of sector 0's middle row has completed
+ * 1: with rows staged (stage_rows 1 or 2), after the neighbours finder's shared-memory
+ * staging of sector 0's middle row has completed
  * (no asynchronous copy is outstanding), its CTA also waits on a barrier that nothing completes,
  * so that bounded wait (1 s of device time) expires and the call reports TPC_ERR_TIMEOUT with
  * stage TPC_STAGE_NEIGHBOURS.  Returns TPC_ERR_INVALID_ARG otherwise. */

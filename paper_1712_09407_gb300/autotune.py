@@ -45,7 +45,7 @@ def time_stages(tracker: Tracker, y, z, row, counts, tuning: dict, repeats: int 
 # The search, in order: (field, candidates, stages whose time decides).
 SPACE = [
     ("bin_occupancy", [0.5, 1.0, 1.5, 2.0, 3.0, 4.0], ["ingest", "neighbours", "construction"]),
-    ("stage_rows", [0, 1], ["neighbours"]),
+    ("stage_rows", [0, 1, 2], ["neighbours"]),
     ("neighbours_block", [64, 128, 256], ["neighbours"]),
     ("construct_block", [64, 96, 128], ["construction"]),
     ("construct_ctas_per_sm", [0, 4, 6, 8, 10, 12], ["construction"]),

@@ -305,6 +305,7 @@ extern "C" int tpc_tracker_set_tuning(tpc_tracker *tr, const tpc_tuning *t)
     if (!(t->bin_occupancy >= 0.5f) || t->neighbours_block < 32 || t->neighbours_block > 256 ||
         t->neighbours_block % 32 || t->construct_block < 32 || t->construct_block > 128 ||
         t->construct_block % 32 || t->construct_ctas_per_sm < 0 || t->construct_mode < 0 || t->construct_mode > 1 ||
+        t->stage_rows < 0 || t->stage_rows > 2 ||
         t->tracklet_capacity < 0 || t->use_graph < 0 || t->use_graph > 1 || t->seed_kernel < -1 ||
         t->seed_kernel > 1 || t->order_group < 0)
         return TPC_ERR_INVALID_ARG;
@@ -746,7 +747,7 @@ static int run(tpc_tracker *tr, const float *y, const float *z, const uint8_t *r
     tr->meta.resize(R);
     tr->dims.resize(R);
     int64_t in_off = 0, s_off = 0, c_off = 0;
-    int smem_need = 0;
+    int smem_need = 0, max_row = 0;
     const float occ = tr->tuning.bin_occupancy;
     for (int64_t u = 0; u < R; u++) {
         const int n = counts[u];
@@ -763,6 +764,7 @@ static int run(tpc_tracker *tr, const float *y, const float *z, const uint8_t *r
         if (nz < 1) nz = 1;
         tr->meta[u] = make_int4((int)in_off, n, (int)s_off, (int)c_off);
         tr->dims[u] = make_int2(ny, nz);
+        if (n > max_row) max_row = n;
         in_off += n;
         s_off += (n + kSlotAlign - 1) / kSlotAlign * kSlotAlign;
         c_off += (ny * nz + 1 + kCellAlign - 1) / kCellAlign * kCellAlign;
@@ -826,6 +828,7 @@ static int run(tpc_tracker *tr, const float *y, const float *z, const uint8_t *r
     lc.n_clusters = n_total;
     lc.n_slots = s_off;
     lc.order_group = tr->tuning.order_group;
+    lc.max_row_clusters = max_row;
 
     // The call's copies, clears and launches go to the caller's stream, or (graph mode) are
     // captured on the tracker's own stream into a graph that updates the cached executable graph

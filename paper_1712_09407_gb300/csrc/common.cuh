@@ -248,6 +248,8 @@ struct LaunchCfg {
     int64_t n_clusters;        // clusters in the call
     int64_t n_slots;           // cluster slots in the call (rows padded)
     int64_t order_group;       // slots per group of the constructor's order (0: one group)
+    int max_row_clusters;      // largest row unit of the call (the cooperative neighbours search packs
+                               // row-relative input indices in 16 bits)
 };
 int launch_ingest(const DevConst &c, const Workspace &w, const float *y, const float *z, const uint8_t *row,
                    int64_t R, cudaStream_t s);

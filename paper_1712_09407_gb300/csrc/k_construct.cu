@@ -9,6 +9,8 @@
 //
 // Floating-point expressions follow the same operation order as the CPU oracle's float mode
 // (the library is compiled without FMA contraction), so both evaluate identical roundings.
+#include <type_traits>
+
 #include "kf.cuh"
 #include "../../include/tpcca.h"
 
@@ -130,11 +132,50 @@ __global__ void __launch_bounds__(256) k_seed(const DevConst c, const Workspace 
 
 constexpr int kSearchBatch = 4;   // candidates whose loads a row search issues together
 
+// Where a lane keeps its filter state between row visits (the state at its last fitted cluster):
+// in registers, or in the CTA's shared memory, one column per thread (conflict-free), which frees
+// about 20 registers for more resident warps.  The prediction of a visit is always in registers.
+constexpr bool kStateInShared = true;
+constexpr int kConstructCtasPerSm = kStateInShared ? 6 : 5;
+
+struct StateRegs {
+    KF s;
+    __device__ __forceinline__ KF get() const { return s; }
+    __device__ __forceinline__ void put(const KF &x) { s = x; }
+};
+
+__device__ __forceinline__ void bind_state(StateRegs &, float (*)[128]) {}
+
+struct StateShared {
+    float (*v)[128];
+    __device__ __forceinline__ KF get() const
+    {
+        const int i = threadIdx.x;
+        KF s;
+        s.p0 = v[0][i]; s.p1 = v[1][i]; s.p2 = v[2][i]; s.p3 = v[3][i]; s.p4 = v[4][i];
+        s.c00 = v[5][i]; s.c10 = v[6][i]; s.c11 = v[7][i]; s.c20 = v[8][i]; s.c21 = v[9][i];
+        s.c22 = v[10][i]; s.c30 = v[11][i]; s.c31 = v[12][i]; s.c32 = v[13][i]; s.c33 = v[14][i];
+        s.c40 = v[15][i]; s.c41 = v[16][i]; s.c42 = v[17][i]; s.c43 = v[18][i]; s.c44 = v[19][i];
+        return s;
+    }
+    __device__ __forceinline__ void put(const KF &s)
+    {
+        const int i = threadIdx.x;
+        v[0][i] = s.p0; v[1][i] = s.p1; v[2][i] = s.p2; v[3][i] = s.p3; v[4][i] = s.p4;
+        v[5][i] = s.c00; v[6][i] = s.c10; v[7][i] = s.c11; v[8][i] = s.c20; v[9][i] = s.c21;
+        v[10][i] = s.c22; v[11][i] = s.c30; v[12][i] = s.c31; v[13][i] = s.c32; v[14][i] = s.c33;
+        v[15][i] = s.c40; v[16][i] = s.c41; v[17][i] = s.c42; v[18][i] = s.c43; v[19][i] = s.c44;
+    }
+};
+
+__device__ __forceinline__ void bind_state(StateShared &s, float (*v)[128]) { s.v = v; }
+
 // Row search and Kalman update of one lane's row visit: the best cluster within the chi2 gate
 // updates the state (and, on the inward pass, is recorded as a hit), otherwise the row is a miss.
 // Returns true when the pass stops (max_miss misses in a row).
+template <class State>
 __device__ __forceinline__ bool search_and_update(const DevConst &c, const Workspace &w, int4 rg, float4 gr, float xr,
-                                                  KF &pr, KF &st, float &xs, int phase, int t, int r, int &rlast,
+                                                  KF &pr, State &st, float &xs, int phase, int t, int r, int &rlast,
                                                   int &miss, int &n, float &chi2sum, int &visits, int &cands)
 {
     visits++;
@@ -153,7 +194,7 @@ __device__ __forceinline__ bool search_and_update(const DevConst &c, const Works
             rlast = r;
         }
         kf_update(pr, g, q.x, q.y);
-        st = pr;
+        st.put(pr);
         xs = xr;
         miss = 0;
         return false;
@@ -164,9 +205,9 @@ __device__ __forceinline__ bool search_and_update(const DevConst &c, const Works
 // After a row visit: the next row of the pass, or the pass's end.  The outward pass turns into
 // the inward pass from its last cluster with a fresh covariance (no cluster: no tracklet); the
 // inward pass writes the tracklet, its state at the innermost fitted cluster.
-template <bool GLOBAL>
+template <bool GLOBAL, class State>
 __device__ __forceinline__ void next_row(const DevConst &c, const Workspace &w, bool stop, int &phase, int t, int &r,
-                                         int rlast, int &miss, int &n, float &chi2sum, KF &st, float xs, int orig0)
+                                         int rlast, int &miss, int &n, float &chi2sum, State &sth, float xs, int orig0)
 {
     if (!stop) {
         r += (phase == 1) ? 1 : -1;
@@ -177,8 +218,10 @@ __device__ __forceinline__ void next_row(const DevConst &c, const Workspace &w, 
             if (rlast < 0) {
                 phase = 0;
             } else {
+                KF st = sth.get();
                 if (GLOBAL) write_outer(w, t, st, xs);   // outer end for global tracking
                 set_seed_cov(st, c);
+                sth.put(st);
                 r = rlast;
                 miss = 0;
                 n = 0;
@@ -186,14 +229,15 @@ __device__ __forceinline__ void next_row(const DevConst &c, const Workspace &w, 
                 phase = 2;
             }
         } else {
-            write_tracklet(c, w, t, st, xs, n, chi2sum, orig0);
+            write_tracklet(c, w, t, sth.get(), xs, n, chi2sum, orig0);
             phase = 0;
         }
     }
 }
 
-// 128 threads and 5 resident CTAs per SM: 96 registers, no spills; with the batched row search
-// this is faster than 6 CTAs at 80 registers (spills) or 4 at up to 128 (measured).
+// 128 threads and kConstructCtasPerSm resident CTAs per SM.  With the state in shared memory:
+// 80 registers, no spills, 6 CTAs (measured 3 % faster than the state in registers at 96
+// registers and 5 CTAs; 7 or 8 CTAs spill and are slower).
 // GLOBAL: also store the outward pass's final state (the outer end for global tracking); a
 // separate instance so that the plain tracker keeps its register allocation.
 // PRESEED selects between two shapes of the same loop (same rows, same arithmetic, same results):
@@ -205,14 +249,16 @@ __device__ __forceinline__ void next_row(const DevConst &c, const Workspace &w, 
 //   transport search together instead of in separate passes of the visit.  Throughput-bound, so
 //   fewer issued instructions win over waiting.
 template <bool GLOBAL, bool PRESEED>
-__global__ void __launch_bounds__(128, 5)
+__global__ void __launch_bounds__(128, kConstructCtasPerSm)
 k_construct(const DevConst c, const Workspace w)
 {
     const int T = n_tracklets(w);
     int phase = 0;            // 0: needs a tracklet, 1: outward pass, 2: inward pass
     int t = 0, sec = 0, r = 0, rlast = -1, miss = 0, n = 0, orig0 = 0;
     float xs = 0.0f, chi2sum = 0.0f;
-    KF st;
+    __shared__ float state_sh[kStateInShared ? 20 : 1][128];   // used when the state lives in shared memory
+    typename std::conditional<kStateInShared, StateShared, StateRegs>::type st;
+    bind_state(st, state_sh);
     int visits = 0, cands = 0;
     if (!PRESEED) {
         while (true) {
@@ -226,7 +272,9 @@ k_construct(const DevConst c, const Workspace w)
                 orig0 = w.orig[sd.x];
                 w.tl_n[t] = 0;
                 w.tl_key[t] = 0ull;
-                if (!seed_tracklet(c, w, sd, st)) continue;
+                KF s0;
+                if (!seed_tracklet(c, w, sd, s0)) continue;
+                st.put(s0);
                 phase = 1;
                 r = r0;
                 xs = c.row_x[r0];
@@ -239,7 +287,7 @@ k_construct(const DevConst c, const Workspace w)
             const int4 rg = __ldg(&w.rgi[unit]);
             const float4 gr = __ldg(&w.grid[unit]);
             const float xr = c.row_x[r];
-            KF pr = st;
+            KF pr = st.get();
             bool stop = false;
             if (xr != xs && !propagate(pr, xr - xs, c)) {
                 stop = true;
@@ -267,12 +315,14 @@ k_construct(const DevConst c, const Workspace w)
                         sec = packed >> 16;
                         r = packed & 0xff;
                         orig0 = __float_as_int(sb.w);
-                        st.p0 = sa.x;
-                        st.p1 = sa.y;
-                        st.p2 = sa.z;
-                        st.p3 = sa.w;
-                        st.p4 = sb.x;
-                        set_seed_cov(st, c);
+                        KF s0;
+                        s0.p0 = sa.x;
+                        s0.p1 = sa.y;
+                        s0.p2 = sa.z;
+                        s0.p3 = sa.w;
+                        s0.p4 = sb.x;
+                        set_seed_cov(s0, c);
+                        st.put(s0);
                         xs = c.row_x[r];
                         rlast = -1;
                         miss = 0;
@@ -282,7 +332,7 @@ k_construct(const DevConst c, const Workspace w)
             }
             if (__all_sync(kFull, phase == 0 && drained)) break;
             // transport to the row (lanes with a tracklet only), then the searching lanes meet
-            KF pr = st;
+            KF pr = st.get();
             int4 rg = make_int4(0, 0, 0, 0);
             float4 gr = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
             float xr = 0.0f;
@@ -327,7 +377,7 @@ int launch_construct(const DevConst &c, const Workspace &w, const LaunchCfg &lc,
     }
     // seed kernel (and the pre-seeded constructor) when the call is expected to give each resident
     // lane at least two tracklets (about one start hit per 20 clusters in central-like events; 5
-    // resident CTAs per SM): two central-like events per call and more
+    // resident CTAs per SM, the threshold measured with): two central-like events per call and more
     const int64_t lanes = (int64_t)lc.num_sms * 5 * lc.construct_block;
     const bool preseed = lc.seed_kernel > 0 || (lc.seed_kernel < 0 && lc.n_clusters / 20 > 2 * lanes);
     // groups of order_group slots, as many as the histogram's kOrderCursors buckets hold

@@ -330,14 +330,223 @@ __device__ __forceinline__ void search_pairs(const DevConst &c, const RowView &U
     }
 }
 
-// 5 CTAs per SM (48 registers): more CTAs overlap one another's row staging (measured 6 % faster than 4)
-__global__ void __launch_bounds__(256, 5)
+// ============================================================================================
+// A2, warp-cooperative search (stage_rows = 2).  A warp takes 32 clusters of row k, one per
+// lane, and every lane finds the slot ranges of its windows in rows k-1 and k+1 (up to four cell
+// rows each) and publishes them in a per-warp table in shared memory.  The candidates of all 32
+// windows are then spread over the lanes: item i of the warp's flattened list goes to lane i mod
+// 32, which finds its owner cluster by a binary search over the table's prefix offsets, tests
+// the owner's window and, if the candidate is inside, appends it to a per-warp list (ballot
+// compaction, in owner order).  The pairs are spread over the owners' row k+1 candidates: a lane
+// takes one u, scores it against each of its owner's row k-1 candidates, keeps the best and
+// offers it to the owner's running minimum with one 64-bit shared-memory atomicMin on (score,
+// input index of u, input index of d; the indices relative to their rows, 16 bits each).  The
+// lane whose offer is the minimum writes the pair's slots.  The best pair is the lexicographic
+// minimum of the same key as in search_pairs, whatever the order, so the links are identical.
+// Rows k-1 and k+1 are the CTA's shared-memory copies (or global memory when they do not fit).
+// A window of more than four cell rows, or more in-window candidates than the lists hold, marks
+// the warp's 32 clusters for k_neighbours_redo.  Rows of 65536 or more clusters use the
+// per-thread form (the host checks).
+// ============================================================================================
+constexpr int kNbCap = 64;       // in-window candidates of one row kept per warp and 32 clusters
+constexpr int kNbRedo = -2;      // link mark of a cluster left to k_neighbours_redo
+
+// Slot ranges of one row inside the window: up to four cell rows along z, relative to the row.
+struct CellRanges {
+    int a0, a1, a2, a3;          // first slot of each cell row's range
+    int p1, p2, p3, n;           // prefix counts: items [0, p1) in range 0, [p1, p2) in 1, ...
+    bool over;                   // the window spans more than four cell rows
+};
+
+struct NbShared {
+    int4 d[kNbCap], u[kNbCap];   // {slot within the row << 5 | owner lane, input index, y bits, z bits}
+    int4 ra_d[32], rp_d[32];     // per lane: row k-1 ranges {a0..a3}, {p1, p2, p3, offset in the warp}
+    int4 ra_u[32], rp_u[32];     // the same for row k+1
+    float2 yz[32];               // per lane: the cluster
+    int cnt_d[32], cnt_u[32];    // in-window candidates per owner
+    int first_d[32];             // first row k-1 candidate of each owner in d
+    unsigned long long best[32]; // per owner: (score bits << 32) | (u index << 16) | d index; ~0: none
+    int b_su[32], b_sd[32];      // the best pair's slots within their rows
+};
+
+__device__ __forceinline__ CellRanges cell_ranges(const RowView &X, float yc, float zc, float wy, float wz)
+{
+    CellRanges r;
+    const int iy0 = cell1(yc - wy - kBinSlack, X.ymin, X.idy, X.ny);
+    const int iy1 = cell1(yc + wy + kBinSlack, X.ymin, X.idy, X.ny);
+    const int iz0 = cell1(zc - wz - kBinSlack, X.zmin, X.idz, X.nz);
+    const int iz1 = cell1(zc + wz + kBinSlack, X.zmin, X.idz, X.nz);
+    const int32_t *c0 = X.cell + iz0 * X.ny;
+    r.a0 = c0[iy0];
+    const int e0 = c0[iy1 + 1];
+    int e1 = 0, e2 = 0, e3 = 0;
+    r.a1 = r.a2 = r.a3 = 0;
+    if (iz1 > iz0) {
+        r.a1 = c0[X.ny + iy0];
+        e1 = c0[X.ny + iy1 + 1];
+    }
+    if (iz1 > iz0 + 1) {
+        r.a2 = c0[2 * X.ny + iy0];
+        e2 = c0[2 * X.ny + iy1 + 1];
+    }
+    if (iz1 > iz0 + 2) {
+        r.a3 = c0[3 * X.ny + iy0];
+        e3 = c0[3 * X.ny + iy1 + 1];
+    }
+    r.over = iz1 > iz0 + 3;
+    r.p1 = e0 - r.a0;
+    r.p2 = r.p1 + (e1 - r.a1);
+    r.p3 = r.p2 + (e2 - r.a2);
+    r.n = r.p3 + (e3 - r.a3);
+    return r;
+}
+
+// Lane holding item i of a warp-flattened list: the last lane whose exclusive offset (rp[l].w)
+// is <= i.
+__device__ __forceinline__ int owner_of(const int4 *rp, int i)
+{
+    int lo = 0;
+#pragma unroll
+    for (int s = 16; s >= 1; s >>= 1)
+        if (rp[lo + s].w <= i) lo += s;              // lo + s <= 31
+    return lo;
+}
+
+// Publishes the lane's ranges of row X and its offset in the warp's flattened list; returns
+// the list's length.
+__device__ __forceinline__ int publish(const CellRanges &cr, int4 *ra, int4 *rp, int lane)
+{
+    const int inc = warp_incl_scan(cr.n);
+    ra[lane] = make_int4(cr.a0, cr.a1, cr.a2, cr.a3);
+    rp[lane] = make_int4(cr.p1, cr.p2, cr.p3, inc - cr.n);
+    return __shfl_sync(kFull, inc, 31);
+}
+
+// The in-window candidates of row X for the warp's 32 clusters, appended to list in owner order
+// with their count per owner.  False (for the whole warp) if they do not fit.
+__device__ __forceinline__ bool gather_row(const RowView &X, int tot, const int4 *ra, const int4 *rp,
+                                           const float2 *yz, float wy, float wz, int4 *list, int *cnt, int lane)
+{
+    int used = 0;
+    for (int base = 0; base < tot; base += 32) {
+        const int i = base + lane;
+        bool pass = false;
+        int4 ent = make_int4(0, 0, 0, 0);
+        int o = 0;
+        if (i < tot) {
+            o = owner_of(rp, i);
+            const int4 a = ra[o], p = rp[o];
+            const float2 co = yz[o];
+            const int r = i - p.w;
+            const int slot = r < p.x ? a.x + r : (r < p.y ? a.y + (r - p.x) : (r < p.z ? a.z + (r - p.y) : a.w + (r - p.z)));
+            const float2 q = X.yz[slot];
+            pass = fabsf(q.x - co.x) <= wy && fabsf(q.y - co.y) <= wz;
+            if (pass) ent = make_int4((slot << 5) | o, X.orig[slot], __float_as_int(q.x), __float_as_int(q.y));
+        }
+        const unsigned m = __ballot_sync(kFull, pass);
+        if (used + __popc(m) > kNbCap) return false;
+        if (pass) {
+            list[used + __popc(m & lanemask_lt())] = ent;
+            atomicAdd(&cnt[o], 1);
+        }
+        used += __popc(m);
+    }
+    return true;
+}
+
+// Links of the warp's 32 clusters (lane: cluster at (yc, zc), v: the lane has one): slots of the
+// best (u, d) pair within the gate, -1 for none, kNbRedo if the warp overflowed.  in_u, in_d:
+// input offsets of rows k+1 and k-1.
+__device__ __forceinline__ void coop_pairs(const DevConst &c, const RowView &U, const RowView &D, int in_u, int in_d,
+                                           NbShared &S, int lane, bool v, float yc, float zc, float wyu, float wzu,
+                                           float wyd, float wzd, float wgt, float gate, int &out_u, int &out_d)
+{
+    CellRanges cd{}, cu{};
+    if (v) {
+        cd = cell_ranges(D, yc, zc, wyd, wzd);
+        cu = cell_ranges(U, yc, zc, wyu, wzu);
+    }
+    out_u = out_d = -1;
+    if (__any_sync(kFull, cd.over || cu.over)) {
+        out_u = out_d = kNbRedo;
+        return;
+    }
+    S.yz[lane] = make_float2(yc, zc);
+    S.cnt_d[lane] = 0;
+    S.cnt_u[lane] = 0;
+    S.best[lane] = ~0ull;
+    const int tot_d = publish(cd, S.ra_d, S.rp_d, lane);
+    const int tot_u = publish(cu, S.ra_u, S.rp_u, lane);
+    __syncwarp();
+    if (!gather_row(D, tot_d, S.ra_d, S.rp_d, S.yz, wyd, wzd, S.d, S.cnt_d, lane) ||
+        !gather_row(U, tot_u, S.ra_u, S.rp_u, S.yz, wyu, wzu, S.u, S.cnt_u, lane)) {
+        out_u = out_d = kNbRedo;
+        __syncwarp();
+        return;
+    }
+    __syncwarp();
+    const int nd = S.cnt_d[lane];
+    S.first_d[lane] = warp_incl_scan(nd) - nd;
+    int n_u = S.cnt_u[lane];
+    n_u = __shfl_sync(kFull, warp_incl_scan(n_u), 31);   // row k+1 candidates of the warp
+    __syncwarp();
+    for (int j = lane; j < n_u; j += 32) {
+        const int4 eu = S.u[j];
+        const int o = eu.x & 31;
+        const int nd_o = S.cnt_d[o], f = S.first_d[o];
+        const float puy = __int_as_float(eu.z), puz = __int_as_float(eu.w);
+        const float2 co = S.yz[o];
+        unsigned long long k = ~0ull;
+        for (int q = f; q < f + nd_o; q++) {
+            const int4 ed = S.d[q];
+            const float pdy = __int_as_float(ed.z), pdz = __int_as_float(ed.w);
+            // residual of c from the chord d -> u, evaluated at x_k (same order as the oracle)
+            const float dy = __fmaf_rn(-(puy - pdy), wgt, co.x - pdy);
+            const float dz = __fmaf_rn(-(puz - pdz), wgt, co.y - pdz);
+            const float sc = __fmaf_rn(dz * dz, c.isz2, (dy * dy) * c.isy2);
+            const unsigned long long kk = ((unsigned long long)__float_as_uint(sc) << 32) |
+                                          ((unsigned long long)(eu.y - in_u) << 16) | (unsigned)(ed.y - in_d);
+            if (kk < k) k = kk;
+        }
+        if (nd_o > 0) atomicMin(&S.best[o], k);
+    }
+    __syncwarp();
+    // the u that won each owner's minimum (each u appears once per owner) writes the pair's slots
+    for (int j = lane; j < n_u; j += 32) {
+        const int4 eu = S.u[j];
+        const int oo = eu.x & 31;
+        const int nd_o = S.cnt_d[oo], f = S.first_d[oo];
+        if (nd_o == 0) continue;
+        const unsigned long long b = S.best[oo];
+        if ((unsigned)((b >> 16) & 0xffff) != (unsigned)(eu.y - in_u)) continue;   // another u won
+        const unsigned dl = (unsigned)(b & 0xffff);
+        for (int q = f; q < f + nd_o; q++)
+            if ((unsigned)(S.d[q].y - in_d) == dl) {
+                S.b_su[oo] = eu.x >> 5;
+                S.b_sd[oo] = S.d[q].x >> 5;
+            }
+    }
+    __syncwarp();
+    const unsigned long long b = S.best[lane];
+    if (v && b != ~0ull && __uint_as_float((uint32_t)(b >> 32)) <= gate) {
+        out_u = U.s_off + S.b_su[lane];
+        out_d = D.s_off + S.b_sd[lane];
+    }
+    __syncwarp();                // the lists are reused by the next 32 clusters
+}
+
+// COOP = false: one thread per cluster (search_pairs); COOP = true: the warp-cooperative search.
+// 5 CTAs per SM for the per-thread form (48 registers): more CTAs overlap one another's row
+// staging (measured 6 % faster than 4).
+template <bool COOP>
+__global__ void __launch_bounds__(256, COOP ? 3 : 5)
 k_neighbours(const DevConst c, const Workspace w, int64_t R, int smem_bytes, int stage)
 {
     extern __shared__ __align__(16) unsigned char sm[];
     __shared__ __align__(8) uint64_t bar;
     __shared__ __align__(8) uint64_t bar_idle;   // test hook: a barrier no copy and no thread completes
     __shared__ int abort_flag;
+    __shared__ NbShared shm[COOP ? 8 : 1];       // the cooperative search's lists, one per warp
     if (threadIdx.x == 0) {
         abort_flag = 0;
         mbar_init(&bar, 1);
@@ -440,14 +649,58 @@ k_neighbours(const DevConst c, const Workspace w, int64_t R, int smem_bytes, int
         const float wgt = dxd / (xu - xd);
         const float om = 1.0f - wgt;
         const float gate = c.gate9 * __fmaf_rn(wgt, wgt, __fmaf_rn(om, om, 1.0f));
-        for (int i = threadIdx.x; i < n; i += blockDim.x) {
+        if (COOP) {
+            const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+            for (int c0 = warp * 32; c0 < n; c0 += blockDim.x) {
+                const int ci = c0 + lane;
+                const bool v = ci < n;
+                float2 pc = make_float2(0.0f, 0.0f);
+                if (v) pc = w.yz[mk.z + ci];
+                int ou, od;
+                coop_pairs(c, U, D, mu.x, md.x, shm[warp], lane, v, pc.x, pc.y, wyu, wzu, wyd, wzd, wgt, gate, ou, od);
+                if (v) {
+                    w.up_raw[mk.z + ci] = ou;
+                    w.dn_raw[mk.z + ci] = od;
+                }
+            }
+        } else {
+            for (int i = threadIdx.x; i < n; i += blockDim.x) {
+                const float2 pc = w.yz[mk.z + i];
+                int ou, od;
+                search_pairs(c, U, D, pc.x, pc.y, wyu, wzu, wyd, wzd, wgt, gate, ou, od);
+                w.up_raw[mk.z + i] = ou;
+                w.dn_raw[mk.z + i] = od;
+            }
+        }
+        __syncthreads();
+    }
+}
+
+// The clusters that the cooperative search left to the per-thread search (windows of more than
+// four cell rows, or more in-window candidates than its lists hold): search_pairs, one thread each.
+__global__ void __launch_bounds__(256) k_neighbours_redo(const DevConst c, const Workspace w, int64_t R)
+{
+    for (int64_t u = blockIdx.x; u < R; u += gridDim.x) {
+        const int4 mk = w.meta[u];
+        for (int i = threadIdx.x; i < mk.y; i += blockDim.x) {
+            if (w.up_raw[mk.z + i] != kNbRedo) continue;
+            const int r = (int)(u % c.nr);
+            const int4 mu = w.meta[u + 1], md = w.meta[u - 1];      // marked clusters have both rows
+            const int2 du = w.dims[u + 1], dd = w.dims[u - 1];
+            const float4 gu = w.grid[u + 1], gd = w.grid[u - 1];
+            const RowView U{w.yz + mu.z, w.orig + mu.z, w.cell + mu.w, gu.x, gu.y, gu.z, gu.w, du.x, du.y, mu.y, mu.z};
+            const RowView D{w.yz + md.z, w.orig + md.z, w.cell + md.w, gd.x, gd.y, gd.z, gd.w, dd.x, dd.y, md.y, md.z};
+            const float xk = c.row_x[r], xu = c.row_x[r + 1], xd = c.row_x[r - 1];
+            const float dxu = xu - xk, dxd = xk - xd;
+            const float wgt = dxd / (xu - xd);
+            const float om = 1.0f - wgt;
+            const float gate = c.gate9 * __fmaf_rn(wgt, wgt, __fmaf_rn(om, om, 1.0f));
             const float2 pc = w.yz[mk.z + i];
             int ou, od;
-            search_pairs(c, U, D, pc.x, pc.y, wyu, wzu, wyd, wzd, wgt, gate, ou, od);
+            search_pairs(c, U, D, pc.x, pc.y, c.ty * dxu, c.tz * dxu, c.ty * dxd, c.tz * dxd, wgt, gate, ou, od);
             w.up_raw[mk.z + i] = ou;
             w.dn_raw[mk.z + i] = od;
         }
-        __syncthreads();
     }
 }
 
@@ -457,12 +710,22 @@ int launch_neighbours(const DevConst &c, const Workspace &w, int64_t R, int smem
                        cudaStream_t s)
 {
     if (R == 0) return 0;
-    int block = lc.neighbours_block;
+    // stage_rows: 0 per-thread search from global memory, 1 the same with rows k +- 1 staged,
+    // 2 cooperative search on staged rows
+    const int mode = (lc.stage_rows == 2 && lc.max_row_clusters >= 65536) ? 1 : lc.stage_rows;
+    const int smem = mode ? smem_bytes : 0;
     int64_t grid = R;
+    if (mode == 2) {
+        if (grid > (int64_t)lc.num_sms * 24) grid = (int64_t)lc.num_sms * 24;
+        if (smem > 48 * 1024 - (int)sizeof(NbShared) * 8)
+            cudaFuncSetAttribute(k_neighbours<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+        k_neighbours<true><<<(unsigned)grid, 256, smem, s>>>(c, w, R, smem, 1);
+        k_neighbours_redo<<<(unsigned)grid, 256, 0, s>>>(c, w, R);
+        return 2;
+    }
     if (grid > (int64_t)lc.num_sms * 64) grid = (int64_t)lc.num_sms * 64;
-    int smem = lc.stage_rows ? smem_bytes : 0;
-    if (smem > 48 * 1024) cudaFuncSetAttribute(k_neighbours, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-    k_neighbours<<<(unsigned)grid, block, smem, s>>>(c, w, R, smem, lc.stage_rows);
+    if (smem > 48 * 1024) cudaFuncSetAttribute(k_neighbours<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    k_neighbours<false><<<(unsigned)grid, lc.neighbours_block, smem, s>>>(c, w, R, smem, mode);
     return 1;
 }
 

@@ -113,7 +113,7 @@ extern "C" int tpc_find_links_noalloc(tpc_tracker *tr, const float *y, const flo
 
     // per row unit metadata, as the allocating path lays it out
     int64_t in_off = 0, s_off = 0, c_off = 0;
-    int smem_need = 0;
+    int smem_need = 0, max_row = 0;
     for (int64_t u = 0; u < R; u++) {
         const int cnt = counts[u];
         const int r = (int)(u % nr);
@@ -129,6 +129,7 @@ extern "C" int tpc_find_links_noalloc(tpc_tracker *tr, const float *y, const flo
         if (nz < 1) nz = 1;
         g_meta[u] = make_int4((int)in_off, cnt, (int)s_off, (int)c_off);
         g_dims[u] = make_int2(ny, nz);
+        if (cnt > max_row) max_row = cnt;
         in_off += cnt;
         s_off += (cnt + kSlotAlign - 1) / kSlotAlign * kSlotAlign;
         c_off += (ny * nz + 1 + kCellAlign - 1) / kCellAlign * kCellAlign;
@@ -157,6 +158,7 @@ extern "C" int tpc_find_links_noalloc(tpc_tracker *tr, const float *y, const flo
     lc.neighbours_block = ti.neighbours_block;
     lc.stage_rows = ti.stage_rows;
     lc.neighbours_smem_max = smem;
+    lc.max_row_clusters = max_row;
     // every launch is checked on its own
     launch_ingest(*ti.dc, w, y, z, row, R, st);
     if (cudaGetLastError() != cudaSuccess) return TPC_ERR_CUDA;

@@ -19,6 +19,7 @@ def main():
     ap.add_argument("--calls", type=int, default=2)
     ap.add_argument("--global-tracking", action="store_true")
     ap.add_argument("--merge", action="store_true")
+    ap.add_argument("--tuning", default="", help="launch choices, e.g. stage_rows=1,construct_mode=1")
     a = ap.parse_args()
     import torch
 
@@ -33,6 +34,8 @@ def main():
     row = torch.cat([p[2] for p in pool]).cuda()
     counts = np.concatenate([p[3] for p in pool])
     tr = Tracker.for_geometry(eventgen.Geometry(), global_tracking=a.global_tracking or None, merge=a.merge or None)
+    if a.tuning:
+        tr.set_tuning({k: (float(v) if "." in v else int(v)) for k, v in (kv.split("=") for kv in a.tuning.split(","))})
     tr.reserve(int(y.shape[0]), a.events, results=1)
     for _ in range(a.calls):
         r = tr.track_batch(y, z, row, counts, a.events)

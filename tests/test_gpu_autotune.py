@@ -16,7 +16,7 @@ pytestmark = pytest.mark.gpu
 
 NARROW = [
     ("bin_occupancy", [0.5, 2.0], ["ingest", "neighbours", "construction"]),
-    ("stage_rows", [0, 1], ["neighbours"]),
+    ("stage_rows", [1, 2], ["neighbours"]),
     ("neighbours_block", [128, 256], ["neighbours"]),
     ("construct_block", [64, 128], ["construction"]),
     ("construct_ctas_per_sm", [0, 6], ["construction"]),

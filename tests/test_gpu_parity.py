@@ -253,7 +253,7 @@ def test_noisy_sector():
 
 
 @pytest.mark.parametrize("tuning", [
-    dict(bin_occupancy=0.5), dict(bin_occupancy=16.0), dict(stage_rows=0),
+    dict(bin_occupancy=0.5), dict(bin_occupancy=16.0), dict(stage_rows=0), dict(stage_rows=2),
     dict(neighbours_block=64, construct_block=64), dict(construct_block=96, construct_ctas_per_sm=1),
     dict(bin_occupancy=2.0, neighbours_block=128, construct_ctas_per_sm=0), dict(construct_mode=1),
     dict(construct_mode=1, bin_occupancy=4.0), dict(use_graph=0), dict(use_graph=0, construct_mode=1),
@@ -362,11 +362,15 @@ def test_budget_is_enforced(ev1):
     tr.close()
 
 
-def test_expired_device_wait_is_reported():
-    """A bounded device wait that runs out (a staging wait for bytes nobody sends, injected from the
-    host) returns TPC_ERR_TIMEOUT; the context stays usable and the next call is correct."""
+@pytest.mark.parametrize("stage_rows", [1, 2])
+def test_expired_device_wait_is_reported(stage_rows):
+    """A bounded device wait that runs out (injected from the host: after a row staging of the
+    neighbours finder has landed, a wait on a barrier that nothing completes, so no copy is in
+    flight) returns TPC_ERR_TIMEOUT; the context stays usable and the next call is correct."""
     ev = _small36()
-    tr, ref, _ = run_gpu(ev, debug=False)
+    tr = Tracker.for_geometry(ev.geometry)
+    tr.set_tuning(dict(stage_rows=stage_rows))
+    tr, ref, _ = run_gpu(ev, tracker=tr, debug=False)
     from paper_1712_09407_gb300.tracker import tpc_tracker_inject
     tpc_tracker_inject(tr.handle, 1)
     y, z, row = to_device(ev)
@@ -418,3 +422,48 @@ def test_clusters_per_track_distribution(both1):
     ho, _ = np.histogram(ref.trk_nhits, bins=bins)
     assert hg.sum() == ho.sum() > 1000
     assert np.array_equal(hg, ho)
+
+
+def _dense_patch_event(seed=7):
+    """Rows 60..66 of sector 0 with 1500 clusters each in an 8 cm x 8 cm patch (tens of in-window
+    candidates per cluster, more than the warp-cooperative search keeps in its lists, so its
+    per-thread fix-up pass runs), plus a sparse central-like background elsewhere."""
+    base = _small36()
+    geo = base.geometry
+    rng = np.random.default_rng(seed)
+    nr = len(geo.row_x)
+    counts = base.counts.reshape(-1, nr).copy()
+    ys, zs, rows = [], [], []
+    off = np.concatenate([[0], np.cumsum(base.counts)])
+    for s in range(counts.shape[0]):
+        for r in range(nr):
+            u = s * nr + r
+            y, z = base.y[off[u]:off[u + 1]], base.z[off[u]:off[u + 1]]
+            if s == 0 and 60 <= r <= 66:
+                y = np.concatenate([y, rng.uniform(0.0, 8.0, 1500).astype(np.float32)])
+                z = np.concatenate([z, rng.uniform(10.0, 18.0, 1500).astype(np.float32)])
+                counts[s, r] += 1500
+            ys.append(y)
+            zs.append(z)
+            rows.append(np.full(len(y), r, np.uint8))
+    import types
+    return types.SimpleNamespace(geometry=geo, y=np.concatenate(ys).astype(np.float32),
+                                 z=np.concatenate(zs).astype(np.float32), row=np.concatenate(rows),
+                                 counts=counts.reshape(-1).astype(np.int32), n=int(counts.sum()))
+
+
+@pytest.mark.parametrize("stage_rows", [2, 1, 0])
+def test_dense_rows_links_equal_oracle(stage_rows):
+    """Links and tracks in very dense rows equal the oracle's in every form of the neighbours finder
+    (the warp-cooperative form sends such clusters to its per-thread fix-up pass)."""
+    ev = _dense_patch_event()
+    ref = run_oracle(ev, key="dense")
+    tr = Tracker.for_geometry(ev.geometry)
+    tr.set_tuning(dict(stage_rows=stage_rows))
+    _, out, dbg = run_gpu(ev, tracker=tr)
+    L = links_as_input_indices(dbg, ev.n)
+    for name in ("up_raw", "dn_raw", "up", "dn"):
+        assert np.array_equal(L[name], getattr(ref, name)), name
+    c = compare_tracks(ev, out, ref)
+    assert c["concordance"] == 1.0 and c["n_exact"] == c["n_matched"] == c["n_ref"]
+    tr.close()
