@@ -224,6 +224,7 @@ class NativeServer:
         if lane_clusters is None:
             lane_clusters = int(hbm_budget / lanes / BYTES_PER_CLUSTER)
         self.keep_results = keep_results           # False: record status and timing only (load tests)
+        self.n_lanes = lanes
         self.lane_clusters = lane_clusters
         self.max_batch = max_batch
         self.handle = tpc_server_create(geometry.row_x, geometry.tan_half, geometry.z_max, geometry.n_sectors,
@@ -262,10 +263,13 @@ class NativeServer:
         return bool(self.inflight)
 
     def warm(self, requests):
-        """A burst of events through every lane before measuring (first-use costs of each lane)."""
-        batch = [r for r in requests[:self.max_batch * 4]]
-        for r in batch:
-            self.submit(dataclasses.replace(r))
+        """Every given event through the server before measuring, so that each lane's first-use
+        costs (its executable graph, its pinned output buffers grown to the largest result) are
+        paid before the first measured arrival: pass the whole event pool the stream draws from.
+        The pool goes through once per lane, so that every lane sees large batches."""
+        for _ in range(self.n_lanes):
+            for r in requests:
+                self.submit(dataclasses.replace(r))
         while self.busy():
             self.poll()
             time.sleep(50e-6)
