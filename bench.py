@@ -59,8 +59,9 @@ def parse():
     ap.add_argument("--no-serving", action="store_true")
     ap.add_argument("--serve-seconds", type=float, default=10.0, help="length of each serving run")
     ap.add_argument("--serve-pool", type=int, default=32, help="events of the batched workload the arrivals draw from")
-    ap.add_argument("--workload", default="central", choices=["central", "batch"],
-                    help="central: the metric's workload (default); batch: 64 events per call vs one at a time")
+    ap.add_argument("--workload", default="central", choices=["central", "batch", "sector", "full"],
+                    help="central: the metric's workload (default); batch: 64 events per call vs one at a time; "
+                         "sector / full: the single-sector (200 tracks) and 36-sector (4000 tracks) events, one per call")
     ap.add_argument("--batch-events", type=int, default=64)
     ap.add_argument("--inflight", type=int, default=2, help="tracker calls on the device at once (one stream each)")
     ap.add_argument("--events-per-call", type=int, default=3,
@@ -851,12 +852,75 @@ def run_batch(args):
     return 0
 
 
+def run_small(args):
+    """The single-sector or the 36-sector event (configs of 200 and 4000 tracks), one event per
+    call: a stream with 2 calls in flight on 2 trackers (12 distinct events, seeds (1, i)), one
+    event at a time (L2 flushed), and the float oracle on the host cores."""
+    import torch
+    from __graft_entry__ import build
+    build()
+    from paper_1712_09407_gb300 import eventgen
+    from paper_1712_09407_gb300.tracker import Tracker
+    cfg = 0 if args.workload == "sector" else 1
+    evs = [eventgen.config_event(cfg, event=i) for i in range(args.resident)]
+    geo = evs[0].geometry
+    dev = [(torch.from_numpy(e.y).cuda(), torch.from_numpy(e.z).cuda(), torch.from_numpy(e.row).cuda(), e.counts)
+           for e in evs]
+    trackers = [Tracker.for_geometry(geo) for _ in range(args.inflight)]
+    for t in trackers:
+        t.reserve(max(e.n for e in evs), 1, results=QDEPTH + 1)
+    streams = [torch.cuda.Stream() for _ in range(args.inflight)]
+
+    def call_1(t, k, s_):
+        d = dev[k % len(dev)]
+        return t.track(d[0], d[1], d[2], d[3], stream=s_)
+
+    st = Streamer(torch, trackers, streams, 1)
+    st.run(max(args.warmup, args.inflight * (QDEPTH + 2)), call_1, timed=False)
+    total_s, launches, _ = st.run(args.steps, call_1, timed=True)
+    flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+    ms = []
+    with torch.cuda.stream(streams[0]):
+        for k in range(min(max(args.steps, 10), 40)):
+            flush.fill_(float(k))
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(streams[0])
+            r = call_1(trackers[0], k, streams[0])
+            b.record(streams[0])
+            r.sync()
+            r.release()
+            ms.append(a.elapsed_time(b))
+    import oracle
+    ocfg = oracle.config_for(geo)
+    oracle.track_event(ocfg, evs[0].y, evs[0].z, evs[0].row, evs[0].counts, precision=32)
+    t0, k = time.perf_counter(), 0
+    while k < 200 and (k < 3 or time.perf_counter() - t0 < 10.0):
+        e = evs[k % len(evs)]
+        oracle.track_event(ocfg, e.y, e.z, e.row, e.counts, precision=32)
+        k += 1
+    n_mean = float(np.mean([e.n for e in evs]))
+    line = {"metric": "events/s", "value": args.steps / total_s, "unit": "events/s", "n_gpus": 1, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": 1e3 * total_s / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": ("single sector (both z halves), 200 primaries, 5% noise" if cfg == 0 else
+                                    "36 sectors, 4000 primaries, 10% noise"), "resident_events": len(evs),
+                       "clusters_per_event": int(round(n_mean)), "inflight_calls": args.inflight},
+            "clusters_per_s": args.steps / total_s * n_mean, "gpu_launches": launches,
+            "one_event_at_a_time": {"ms_per_event": float(np.median(ms)), "l2": "flushed before every event"},
+            "cpu_baseline": {"value": k / (time.perf_counter() - t0), "unit": "events/s", "cores": os.cpu_count(),
+                             "kind": "oracle", "sample": "%d events, float-mode C oracle, OpenMP over sectors" % k}}
+    print(json.dumps(line))
+    return 0
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         return run_reference(args)
     if args.workload == "batch":
         return run_batch(args)
+    if args.workload in ("sector", "full"):
+        return run_small(args)
     return run_ours(args)
 
 
