@@ -147,8 +147,8 @@ __device__ int prolong(const DevConst &c, const Workspace &w, int p, int sec, co
         const Gain g = residual_cov_inv(q, c);
         float chi2 = 0.0f;
         float2 m;
-        const int bl = search_cells(c, w.yz + rg.x, w.orig + rg.x, w.cell + rg.y, gr, rg.z, rg.w, q, g, chi2, m, cands,
-                                    w.used + rg.x);
+        const int bl = search_cells_mlp<4, true>(c, w.yz + rg.x, w.orig + rg.x, w.cell + rg.y, gr, rg.z, rg.w, q, g,
+                                                 chi2, cands, w.used + rg.x, &m);
         if (bl >= 0 && chi2 <= c.chi2max) {
             const int b = rg.x + bl;
             chi2sum = chi2sum + chi2;

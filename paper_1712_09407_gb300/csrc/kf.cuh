@@ -292,12 +292,14 @@ __device__ __forceinline__ int search_cells(const DevConst &c, const float2 *yz,
 // (windows wider than three cells in z, rare) follow one at a time.  The best cluster is the
 // lexicographic minimum of (chi2, input index) over the same candidates, whatever order they are
 // offered in, so the result is identical to search_cells.  Statistics: ncand counts the clusters
-// of every enumerated cell, as there.
-template <int CB>
+// of every enumerated cell, as there.  USED: clusters with a nonzero byte in used are skipped and
+// the best cluster's (y, z) is returned in best_yz (global tracking); otherwise best_yz is left.
+template <int CB, bool USED = false>
 __device__ __forceinline__ int search_cells_mlp(const DevConst &c, const float2 *__restrict__ yz,
                                                 const int32_t *__restrict__ orig, const int32_t *__restrict__ cell,
                                                 const float4 gr, int ny, int nz, const KF &pr, const Gain &g,
-                                                float &chi2_out, int &ncand)
+                                                float &chi2_out, int &ncand, const uint8_t *__restrict__ used = nullptr,
+                                                float2 *best_yz = nullptr)
 {
     const float wy = c.nsig * sqrtf(pr.c00 + c.sy2);
     const float wz = c.nsig * sqrtf(pr.c11 + c.sz2);
@@ -328,11 +330,15 @@ __device__ __forceinline__ int search_cells_mlp(const DevConst &c, const float2 
             const int i = i0 + k;
             sl[k] = i < n0 ? a0 + i : (i < n01 ? a1 + (i - n0) : a2 + (i - n01));
         }
-#pragma unroll
-        for (int k = 0; k < CB; k++) q[k] = i0 + k < n ? __ldg(yz + sl[k]) : make_float2(0.0f, 0.0f);
+        uint8_t uk[CB];
 #pragma unroll
         for (int k = 0; k < CB; k++) {
-            if (i0 + k < n && fabsf(q[k].x - y) <= wy && fabsf(q[k].y - z) <= wz)
+            q[k] = i0 + k < n ? __ldg(yz + sl[k]) : make_float2(0.0f, 0.0f);
+            if (USED) uk[k] = i0 + k < n ? __ldg(used + sl[k]) : (uint8_t)1;
+        }
+#pragma unroll
+        for (int k = 0; k < CB; k++) {
+            if (i0 + k < n && (!USED || !uk[k]) && fabsf(q[k].x - y) <= wy && fabsf(q[k].y - z) <= wz)
                 b.offer(sl[k], q[k], chi2_of(g, q[k].x - y, q[k].y - z), orig);
         }
     }
@@ -340,11 +346,13 @@ __device__ __forceinline__ int search_cells_mlp(const DevConst &c, const float2 
         const int a = __ldg(cell + iz * ny + iy0), e = __ldg(cell + iz * ny + iy1 + 1);
         ncand += e - a;
         for (int k = a; k < e; k++) {
+            if (USED && __ldg(used + k)) continue;
             const float2 q = __ldg(yz + k);
             if (fabsf(q.x - y) <= wy && fabsf(q.y - z) <= wz) b.offer(k, q, chi2_of(g, q.x - y, q.y - z), orig);
         }
     }
     chi2_out = b.bc;
+    if (USED) *best_yz = b.bq;
     return b.best;
 }
 
