@@ -67,6 +67,7 @@ def parse():
     ap.add_argument("--events-per-call", type=int, default=3,
                     help="central events tracked by one call (tpc_track_batch); a step is one call")
     ap.add_argument("--resident", type=int, default=12, help="distinct resident central events (> L2 together)")
+    ap.add_argument("--tuning", default="", help="launch choices for every tracker, e.g. construct_block=64")
     return ap.parse_args()
 
 
@@ -357,9 +358,16 @@ def run_reference(args):
 # ------------------------------------------------------------------------------------------------
 # our arm
 # ------------------------------------------------------------------------------------------------
-QDEPTH = 6     # calls each tracker has outstanding in the streamed legs (its result ring holds one more)
+QDEPTH = 16    # calls each tracker has outstanding in the streamed legs (its result ring holds one more): about
+              # 120 ms of queued device work over two streams, so that a host pause does not starve the device
 PREROLL_CYCLES = 10_000_000   # about 5 ms at 2 GHz
 STAGES = ["setup", "ingest", "neighbours", "evolution", "construction", "selection", "output", "global", "merge"]
+
+
+def apply_tuning(tracker, spec):
+    """Launch choices from a "field=value,..." string (none: the library's defaults)."""
+    if spec:
+        tracker.set_tuning({k: (float(v) if "." in v else int(v)) for k, v in (kv.split("=") for kv in spec.split(","))})
 
 
 class Streamer:
@@ -460,9 +468,11 @@ def run_ours(args):
     # tracker's workspace and result buffers are allocated here, so the timed calls allocate nothing
     trackers = [Tracker.for_geometry(geo) for _ in range(args.inflight)]
     for t in trackers:
+        apply_tuning(t, args.tuning)
         t.reserve(max(c_["n"] for c_ in calls), B, results=QDEPTH + 1)
     trackers1 = [Tracker.for_geometry(geo) for _ in range(args.inflight)]
     for t in trackers1:
+        apply_tuning(t, args.tuning)
         t.reserve(max(p[4] for p in pool), 1, results=QDEPTH + 1)
     streams = [torch.cuda.Stream() for _ in range(args.inflight)]
     stream = streams[0]
@@ -640,6 +650,7 @@ def run_ours(args):
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": workload_config(len(pool), n_mean, world),
             "launch": {"events_per_call": B, "inflight_calls": args.inflight, "calls_outstanding_per_tracker": QDEPTH,
+                       "tuning": args.tuning or "library defaults",
                        "warmup_calls": n_warm, "allocation": "workspace and %d result buffers per tracker "
                                                              "preallocated (tpc_tracker_reserve_results)" % (QDEPTH + 1)},
             "clusters_per_s": value * n_mean, "tracks_per_event": int(np.mean(tracks)),
