@@ -144,31 +144,34 @@ struct StateRegs {
     __device__ __forceinline__ void put(const KF &x) { s = x; }
 };
 
-__device__ __forceinline__ void bind_state(StateRegs &, float (*)[128]) {}
+__device__ __forceinline__ void bind_state(StateRegs &, float *) {}
+
+// One thread's 20 floats at a stride of kStateStride floats per thread: with an odd stride the 32
+// lanes of a warp fall in 32 different banks, and each field sits at a constant offset from the
+// thread's base.  The array is the launch's dynamic shared memory, sized to the block.
+constexpr int kStateStride = 21;
 
 struct StateShared {
-    float (*v)[128];
+    float *v;
     __device__ __forceinline__ KF get() const
     {
-        const int i = threadIdx.x;
         KF s;
-        s.p0 = v[0][i]; s.p1 = v[1][i]; s.p2 = v[2][i]; s.p3 = v[3][i]; s.p4 = v[4][i];
-        s.c00 = v[5][i]; s.c10 = v[6][i]; s.c11 = v[7][i]; s.c20 = v[8][i]; s.c21 = v[9][i];
-        s.c22 = v[10][i]; s.c30 = v[11][i]; s.c31 = v[12][i]; s.c32 = v[13][i]; s.c33 = v[14][i];
-        s.c40 = v[15][i]; s.c41 = v[16][i]; s.c42 = v[17][i]; s.c43 = v[18][i]; s.c44 = v[19][i];
+        s.p0 = v[0]; s.p1 = v[1]; s.p2 = v[2]; s.p3 = v[3]; s.p4 = v[4];
+        s.c00 = v[5]; s.c10 = v[6]; s.c11 = v[7]; s.c20 = v[8]; s.c21 = v[9];
+        s.c22 = v[10]; s.c30 = v[11]; s.c31 = v[12]; s.c32 = v[13]; s.c33 = v[14];
+        s.c40 = v[15]; s.c41 = v[16]; s.c42 = v[17]; s.c43 = v[18]; s.c44 = v[19];
         return s;
     }
     __device__ __forceinline__ void put(const KF &s)
     {
-        const int i = threadIdx.x;
-        v[0][i] = s.p0; v[1][i] = s.p1; v[2][i] = s.p2; v[3][i] = s.p3; v[4][i] = s.p4;
-        v[5][i] = s.c00; v[6][i] = s.c10; v[7][i] = s.c11; v[8][i] = s.c20; v[9][i] = s.c21;
-        v[10][i] = s.c22; v[11][i] = s.c30; v[12][i] = s.c31; v[13][i] = s.c32; v[14][i] = s.c33;
-        v[15][i] = s.c40; v[16][i] = s.c41; v[17][i] = s.c42; v[18][i] = s.c43; v[19][i] = s.c44;
+        v[0] = s.p0; v[1] = s.p1; v[2] = s.p2; v[3] = s.p3; v[4] = s.p4;
+        v[5] = s.c00; v[6] = s.c10; v[7] = s.c11; v[8] = s.c20; v[9] = s.c21;
+        v[10] = s.c22; v[11] = s.c30; v[12] = s.c31; v[13] = s.c32; v[14] = s.c33;
+        v[15] = s.c40; v[16] = s.c41; v[17] = s.c42; v[18] = s.c43; v[19] = s.c44;
     }
 };
 
-__device__ __forceinline__ void bind_state(StateShared &s, float (*v)[128]) { s.v = v; }
+__device__ __forceinline__ void bind_state(StateShared &s, float *base) { s.v = base + threadIdx.x * kStateStride; }
 
 // Row search and Kalman update of one lane's row visit: the best cluster within the chi2 gate
 // updates the state (and, on the inward pass, is recorded as a hit), otherwise the row is a miss.
@@ -256,9 +259,9 @@ k_construct(const DevConst c, const Workspace w)
     int phase = 0;            // 0: needs a tracklet, 1: outward pass, 2: inward pass
     int t = 0, sec = 0, r = 0, rlast = -1, miss = 0, n = 0, orig0 = 0;
     float xs = 0.0f, chi2sum = 0.0f;
-    __shared__ float state_sh[kStateInShared ? 20 : 1][128];   // used when the state lives in shared memory
+    extern __shared__ float construct_state[];   // blockDim.x * kStateStride floats with the state in shared memory
     typename std::conditional<kStateInShared, StateShared, StateRegs>::type st;
-    bind_state(st, state_sh);
+    bind_state(st, construct_state);
     int visits = 0, cands = 0;
     if (!PRESEED) {
         while (true) {
@@ -369,10 +372,11 @@ k_construct(const DevConst c, const Workspace w)
 int launch_construct(const DevConst &c, const Workspace &w, const LaunchCfg &lc, cudaStream_t s)
 {
     int per_sm = lc.construct_ctas_per_sm;
+    const size_t state_bytes = kStateInShared ? (size_t)lc.construct_block * kStateStride * sizeof(float) : 0;
     if (per_sm <= 0) {
         int occ = 0;
         cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, c.global ? k_construct<true, false> : k_construct<false, false>,
-                                                      lc.construct_block, 0);
+                                                      lc.construct_block, state_bytes);
         per_sm = occ > 0 ? occ : 1;
     }
     // seed kernel (and the pre-seeded constructor) when the call is expected to give each resident
@@ -395,11 +399,11 @@ int launch_construct(const DevConst &c, const Workspace &w, const LaunchCfg &lc,
     if (preseed) k_seed<<<lc.num_sms * 8, 256, 0, s>>>(c, w);
     const unsigned grid = lc.num_sms * per_sm;
     if (c.global) {
-        if (preseed) k_construct<true, true><<<grid, lc.construct_block, 0, s>>>(c, w);
-        else k_construct<true, false><<<grid, lc.construct_block, 0, s>>>(c, w);
+        if (preseed) k_construct<true, true><<<grid, lc.construct_block, state_bytes, s>>>(c, w);
+        else k_construct<true, false><<<grid, lc.construct_block, state_bytes, s>>>(c, w);
     } else {
-        if (preseed) k_construct<false, true><<<grid, lc.construct_block, 0, s>>>(c, w);
-        else k_construct<false, false><<<grid, lc.construct_block, 0, s>>>(c, w);
+        if (preseed) k_construct<false, true><<<grid, lc.construct_block, state_bytes, s>>>(c, w);
+        else k_construct<false, false><<<grid, lc.construct_block, state_bytes, s>>>(c, w);
     }
     return preseed ? 5 : 4;
 }
