@@ -379,9 +379,11 @@ int launch_construct(const DevConst &c, const Workspace &w, const LaunchCfg &lc,
                                                       lc.construct_block, state_bytes);
         per_sm = occ > 0 ? occ : 1;
     }
-    // seed kernel (and the pre-seeded constructor) when the call is expected to give each resident
-    // lane at least two tracklets (about one start hit per 20 clusters in central-like events; 5
-    // resident CTAs per SM, the threshold measured with): two central-like events per call and more
+    // seed kernel (and the pre-seeded constructor) when the call has more than 40 clusters per lane
+    // of 5 CTAs per SM (about one start hit per 20 clusters in central-like events, so two tracklets
+    // per such lane).  With 64-thread CTAs that is 1.95 M clusters: one central-like event (3.3 M)
+    // takes the pre-seeded form, measured 1.29 against 1.37 ms for its construction stage; with
+    // 128-thread CTAs, two central-like events per call and more
     const int64_t lanes = (int64_t)lc.num_sms * 5 * lc.construct_block;
     const bool preseed = lc.seed_kernel > 0 || (lc.seed_kernel < 0 && lc.n_clusters / 20 > 2 * lanes);
     // groups of order_group slots, as many as the histogram's kOrderCursors buckets hold
