@@ -362,6 +362,7 @@ static size_t carve(tpc_tracker *tr, const WsSizes &s, Alloc &a)
     w.tl_w = a.take<float>(s.T);
     w.tl_key = a.take<unsigned long long>(s.T);
     w.tl_nowned = a.take<int32_t>(s.T);
+    w.tl_own = a.take<uint32_t>(s.T * ((tr->n_rows + 31) / 32));
     w.tl_inner = a.take<int32_t>(s.T);
     if (tr->dc.global) {
         w.tl_opar = a.take<float>(5 * s.T);

@@ -103,6 +103,7 @@ struct Workspace {
     float *tl_x, *tl_chi2, *tl_w;
     unsigned long long *tl_key;
     int32_t *tl_nowned;
+    uint32_t *tl_own;      // [tcap * ((nr + 31) / 32)] bit i of word i / 32: the tracklet owns its hit i
     int32_t *tl_inner;     // input index of the innermost owned cluster, -1 if rejected
     // global tracking (Section 5)
     float *tl_opar, *tl_ocov, *tl_ox;   // outward pass's state at its last cluster [5|15|1][tcap]

@@ -734,57 +734,92 @@ int launch_neighbours(const DevConst &c, const Workspace &w, int64_t R, int smem
 // kept up link, no kept down link and a chain of >= min_chain clusters; its record holds the
 // chain's first cluster and its length counted up to max(min_chain, 4).
 // ============================================================================================
-__global__ void __launch_bounds__(256) k_evolve(const DevConst c, const Workspace w, int64_t R)
+// One CTA per row unit, kEvolvePer clusters per thread in one pass (1024 per pass): the loads of
+// all its clusters' links are issued together, then those of their partners, so that a pass waits
+// for two round trips; the start candidates (kept up link, no kept down link) are gathered in
+// shared memory and their chains are walked together afterwards, the next link's up index loaded
+// with the current link's test, so that the walk waits for need - 1 more round trips per pass
+// (need = max(min_chain, 4)) instead of each warp walking its chains in turn.
+constexpr int kEvolveThreads = 256;
+constexpr int kEvolvePer = 4;
+
+__global__ void __launch_bounds__(kEvolveThreads) k_evolve(const DevConst c, const Workspace w, int64_t R)
 {
+    __shared__ int2 cand[kEvolveThreads * kEvolvePer];   // (candidate cluster, its kept up link)
+    __shared__ int ncand;
     const int lane = threadIdx.x & 31;
+    const int need = c.min_chain > 4 ? c.min_chain : 4;
     for (int64_t u = blockIdx.x; u < R; u += gridDim.x) {
         const int4 m = w.meta[u];
         const int n = m.y;
         const int r = (int)(u % c.nr);
         const int sec = (int)(u / c.nr);
-        for (int i0 = 0; i0 < n; i0 += blockDim.x) {
-            const int i = i0 + threadIdx.x;
-            const bool v = i < n;
-            int first = -1, clen = 0;
-            bool is_start = false;
-            if (v) {
-                const int cl = m.z + i;
-                const int u1 = w.up_raw[cl], d1 = w.dn_raw[cl];
-                const int upk = (u1 >= 0 && w.dn_raw[u1] == cl) ? u1 : -1;
-                const int dnk = (d1 >= 0 && w.up_raw[d1] == cl) ? d1 : -1;
-                w.up[cl] = upk;
-                w.dn[cl] = dnk;
-                if (upk >= 0 && dnk < 0) {
-                    // chain length, counted only as far as the start test and the work order need
-                    // (min_chain, and >= 4 for the constructor's ordering key); the constructor walks
-                    // the whole chain for its seed
-                    const int need = c.min_chain > 4 ? c.min_chain : 4;
-                    int len = 1, t = cl;
-                    while (len < need) {
-                        const int nx = w.up_raw[t];
-                        if (nx < 0 || w.dn_raw[nx] != t) break;
+        for (int i0 = 0; i0 < n; i0 += kEvolveThreads * kEvolvePer) {
+            if (threadIdx.x == 0) ncand = 0;
+            __syncthreads();
+            int cl[kEvolvePer], u1[kEvolvePer], d1[kEvolvePer], bu[kEvolvePer], bd[kEvolvePer];
+#pragma unroll
+            for (int k = 0; k < kEvolvePer; k++) {
+                const int i = i0 + k * kEvolveThreads + threadIdx.x;
+                cl[k] = i < n ? m.z + i : -1;
+                u1[k] = cl[k] >= 0 ? w.up_raw[cl[k]] : -1;
+                d1[k] = cl[k] >= 0 ? w.dn_raw[cl[k]] : -1;
+            }
+#pragma unroll
+            for (int k = 0; k < kEvolvePer; k++) {
+                bu[k] = u1[k] >= 0 ? w.dn_raw[u1[k]] : -1;      // down link of the up partner
+                bd[k] = d1[k] >= 0 ? w.up_raw[d1[k]] : -1;      // up link of the down partner
+            }
+#pragma unroll
+            for (int k = 0; k < kEvolvePer; k++) {
+                if (cl[k] < 0) continue;
+                const int upk = (u1[k] >= 0 && bu[k] == cl[k]) ? u1[k] : -1;
+                const int dnk = (d1[k] >= 0 && bd[k] == cl[k]) ? d1[k] : -1;
+                w.up[cl[k]] = upk;
+                w.dn[cl[k]] = dnk;
+                if (upk >= 0 && dnk < 0) cand[atomicAdd(&ncand, 1)] = make_int2(cl[k], upk);
+            }
+            __syncthreads();
+            // chain length of each candidate, counted only as far as the start test and the work
+            // order need (min_chain, and >= 4 for the constructor's ordering key); the candidate and
+            // its up link are the chain's first two clusters
+            const int nc = ncand;
+            for (int j0 = 0; j0 < nc; j0 += kEvolveThreads) {
+                const int j = j0 + threadIdx.x;
+                int first = -1, clen = 0;
+                bool is_start = false;
+                if (j < nc) {
+                    const int2 e = cand[j];
+                    int t = e.y, len = 2;
+                    int nx = len < need ? w.up_raw[t] : -1;
+                    while (len < need && nx >= 0) {
+                        const int back = w.dn_raw[nx];
+                        const int nn = len + 1 < need ? w.up_raw[nx] : -1;
+                        if (back != t) break;
                         t = nx;
                         len++;
+                        nx = nn;
                     }
                     if (len >= c.min_chain) {
                         is_start = true;
                         clen = len;
-                        first = cl;
+                        first = e.x;
+                    }
+                }
+                const unsigned mask = __ballot_sync(kFull, is_start);
+                int base = 0;
+                if (lane == 0 && mask) base = atomicAdd(&w.counters[CNT_STARTS], __popc(mask));
+                base = __shfl_sync(kFull, base, 0);
+                if (is_start) {
+                    const int slot = base + __popc(mask & lanemask_lt());
+                    if (slot < w.tlim) {
+                        w.starts[slot] = make_int4(first, -1, -1, (sec << 16) | (clen << 8) | r);
+                    } else {
+                        set_error(w.err, TPC_ERR_CAPACITY, (int)u, c, TPC_STAGE_EVOLUTION);
                     }
                 }
             }
-            const unsigned mask = __ballot_sync(kFull, is_start);
-            int base = 0;
-            if (lane == 0 && mask) base = atomicAdd(&w.counters[CNT_STARTS], __popc(mask));
-            base = __shfl_sync(kFull, base, 0);
-            if (is_start) {
-                const int slot = base + __popc(mask & lanemask_lt());
-                if (slot < w.tlim) {
-                    w.starts[slot] = make_int4(first, -1, -1, (sec << 16) | (clen << 8) | r);
-                } else {
-                    set_error(w.err, TPC_ERR_CAPACITY, (int)u, c, TPC_STAGE_EVOLUTION);
-                }
-            }
+            __syncthreads();      // cand and ncand are reused by the next pass
         }
     }
 }
@@ -793,7 +828,7 @@ int launch_evolve(const DevConst &c, const Workspace &w, int64_t R, cudaStream_t
 {
     if (R == 0) return 0;
     int64_t grid = R < 65535 * 4 ? R : 65535 * 4;
-    k_evolve<<<(unsigned)grid, 128, 0, s>>>(c, w, R);
+    k_evolve<<<(unsigned)grid, kEvolveThreads, 0, s>>>(c, w, R);
     return 1;
 }
 

@@ -177,6 +177,7 @@ __global__ void __launch_bounds__(256) k_count(const DevConst c, const Workspace
             const int i = i0 + lane;
             const bool own = i < n && w.ckey[h[i]] == key;
             const unsigned mask = __ballot_sync(kFull, own);
+            if (lane == 0) w.tl_own[(int64_t)t * ((c.nr + 31) >> 5) + (i0 >> 5)] = mask;   // for the output
             owned += __popc(mask);
             if (mask) inner_i = i0 + 31 - __clz(mask);   // hits run outer to inner
         }
@@ -251,7 +252,6 @@ __global__ void __launch_bounds__(256) k_write(const DevConst c, const Workspace
         if (!TPC_IDX(m, o.mcap, w.err, c, 6)) continue;
         const int t = w.rank_trk[m];
         const int first = w.rank_first[m];
-        const unsigned long long key = w.tl_key[t];
         const int n = w.tl_n[t];
         const int32_t *h = w.tl_hits + (int64_t)t * c.nr;
         // with global tracking, an inward prolongation that fitted clusters gives the state
@@ -285,10 +285,12 @@ __global__ void __launch_bounds__(256) k_write(const DevConst c, const Workspace
         // failed (a full prolongation pool leaves holes in it)
         const bool gok = c.global && w.err[ERR_STATUS] == 0;
         if (gok) pos = write_prolongation(w, o, 2 * t, pos, true);
-        // owned clusters, inner to outer (the tracklet stores them outer to inner)
+        // owned clusters, inner to outer (the tracklet stores them outer to inner), from the
+        // ownership bits of the count
+        const uint32_t *om = w.tl_own + (int64_t)t * ((c.nr + 31) >> 5);
         for (int i0 = 0; i0 < n; i0 += 32) {
             const int i = n - 1 - (i0 + lane);
-            const bool own = i >= 0 && w.ckey[h[i]] == key;
+            const bool own = i >= 0 && ((om[i >> 5] >> (i & 31)) & 1u);
             const unsigned mask = __ballot_sync(kFull, own);
             if (own && TPC_IDX(pos + __popc(mask & lanemask_lt()), o.hcap, w.err, c, 6))
             o.hits[pos + __popc(mask & lanemask_lt())] = w.orig[h[i]];
