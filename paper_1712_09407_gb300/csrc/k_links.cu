@@ -12,9 +12,15 @@ namespace tpc {
 
 // ============================================================================================
 // A1: per (event, sector, row) unit: y/z extent, grid, counting sort into padded slots.
-// One warp per row unit; the sort is stable in input order.
+// One warp per row unit; the sort is stable in input order.  The first pass over the row's
+// clusters also copies their (y, z) into the warp's shared memory (rows of up to kIngestStage
+// clusters), so that the histogram and scatter passes read them there instead of from L2
+// (3-event call 0.186 -> 0.160 ms; 768 against 1024 staged clusters leaves room for 5 CTAs per
+// SM instead of 4 and was the faster of the two).
 // ============================================================================================
 constexpr int kIngestWarps = 4;
+constexpr int kIngestStage = 768;
+constexpr int kIngestWarpInts = kCellMax + 2 * kIngestStage;   // histogram, then the staged (y, z)
 
 __global__ void __launch_bounds__(kIngestWarps * 32)
 k_ingest(const DevConst c, const Workspace w, const float *__restrict__ yin, const float *__restrict__ zin,
@@ -22,7 +28,8 @@ k_ingest(const DevConst c, const Workspace w, const float *__restrict__ yin, con
 {
     extern __shared__ int sh_hist[];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    int *hist = sh_hist + warp * kCellMax;
+    int *hist = sh_hist + warp * kIngestWarpInts;
+    float2 *syz = (float2 *)(hist + kCellMax);
     for (int64_t u = (int64_t)blockIdx.x * kIngestWarps + warp; u < R; u += (int64_t)gridDim.x * kIngestWarps) {
         const int4 m = w.meta[u];
         const int2 d = w.dims[u];
@@ -31,8 +38,11 @@ k_ingest(const DevConst c, const Workspace w, const float *__restrict__ yin, con
         const int r = (int)(u % c.nr);
         float ymin = FLT_MAX, ymax = -FLT_MAX, zmin = FLT_MAX, zmax = -FLT_MAX;
         int bad = 0;
+        const bool staged = n <= kIngestStage;
+#pragma unroll 4
         for (int i = lane; i < n; i += 32) {
             float y = __ldg(yin + in_off + i), z = __ldg(zin + in_off + i);
+            if (staged) syz[i] = make_float2(y, z);
             ymin = fminf(ymin, y);
             ymax = fmaxf(ymax, y);
             zmin = fminf(zmin, z);
@@ -61,8 +71,8 @@ k_ingest(const DevConst c, const Workspace w, const float *__restrict__ yin, con
         for (int j = lane; j < nc; j += 32) hist[j] = 0;
         __syncwarp();
         for (int i = lane; i < n; i += 32) {
-            float y = __ldg(yin + in_off + i), z = __ldg(zin + in_off + i);
-            int cc = cell1(z, zmin, idz, nz) * ny + cell1(y, ymin, idy, ny);
+            const float2 q = staged ? syz[i] : make_float2(__ldg(yin + in_off + i), __ldg(zin + in_off + i));
+            int cc = cell1(q.y, zmin, idz, nz) * ny + cell1(q.x, ymin, idy, ny);
             atomicAdd(&hist[cc], 1);
         }
         __syncwarp();
@@ -85,8 +95,9 @@ k_ingest(const DevConst c, const Workspace w, const float *__restrict__ yin, con
             float y = 0.0f, z = 0.0f;
             int cc = -1 - lane;                       // distinct sentinel for idle lanes
             if (v) {
-                y = __ldg(yin + in_off + i);
-                z = __ldg(zin + in_off + i);
+                const float2 q = staged ? syz[i] : make_float2(__ldg(yin + in_off + i), __ldg(zin + in_off + i));
+                y = q.x;
+                z = q.y;
                 cc = cell1(z, zmin, idz, nz) * ny + cell1(y, ymin, idy, ny);
             }
             const unsigned peers = __match_any_sync(kFull, cc);
@@ -110,7 +121,7 @@ int launch_ingest(const DevConst &c, const Workspace &w, const float *y, const f
     if (R == 0) return 0;
     int64_t blocks = (R + kIngestWarps - 1) / kIngestWarps;
     if (blocks > 65535LL * 8) blocks = 65535LL * 8;
-    k_ingest<<<(unsigned)blocks, kIngestWarps * 32, kIngestWarps * kCellMax * sizeof(int), s>>>(c, w, y, z, row, R);
+    k_ingest<<<(unsigned)blocks, kIngestWarps * 32, kIngestWarps * kIngestWarpInts * sizeof(int), s>>>(c, w, y, z, row, R);
     return 1;
 }
 
