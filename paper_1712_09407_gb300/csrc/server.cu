@@ -120,7 +120,13 @@ struct tpc_server {
     std::atomic<bool> stop{false};
     std::thread th;
     std::vector<HostOut> retired;      // outgrown pinned result buffers (server thread only)
+    // Released requests, kept with the capacity of their result vectors (guarded by mu), so that a
+    // steady stream of events allocates no host memory per event once the largest results have
+    // been seen (large vectors would otherwise be mapped and unmapped for every event).
+    std::vector<Req *> spare;
 };
+
+constexpr size_t kSpareMax = 64;       // requests kept for reuse; beyond that they are freed
 
 namespace {
 
@@ -339,13 +345,26 @@ extern "C" int tpc_server_submit(tpc_server *s, const float *y, const float *z, 
         sum += counts[u];
     }
     if (sum != n) return TPC_ERR_INVALID_ARG;
-    Req *r = new (std::nothrow) Req();
+    Req *r = nullptr;
+    {
+        std::lock_guard<std::mutex> g(s->mu);
+        if (!s->spare.empty()) {
+            r = s->spare.back();
+            s->spare.pop_back();
+        }
+    }
+    if (!r) r = new (std::nothrow) Req();
     if (!r) return TPC_ERR_CUDA;
     r->y = y;
     r->z = z;
     r->row = row;
     r->n = n;
     r->counts.assign(counts, counts + s->n_units);
+    r->t_launch = r->t_done = 0;
+    r->status = TPC_OK;
+    r->batch = 0;
+    for (auto *v : {&r->par, &r->cov, &r->x, &r->alpha, &r->chi2}) v->clear();      // capacity kept
+    for (auto *v : {&r->ndf, &r->nhits, &r->first, &r->sector, &r->hits}) v->clear();
     r->t_submit = now_ns();
     {
         std::lock_guard<std::mutex> g(s->mu);
@@ -411,6 +430,10 @@ extern "C" int tpc_server_release(tpc_server *s, int64_t id)
         r = it->second;
         if (r->t_done == 0) return TPC_ERR_STATE;
         s->reqs.erase(it);
+        if (s->spare.size() < kSpareMax) {
+            s->spare.push_back(r);
+            r = nullptr;
+        }
     }
     delete r;
     return TPC_OK;
@@ -436,5 +459,6 @@ extern "C" void tpc_server_destroy(tpc_server *s)
     }
     for (HostOut &o : s->retired) free_out(o);
     for (auto &kv : s->reqs) delete kv.second;
+    for (Req *r : s->spare) delete r;
     delete s;
 }
