@@ -562,6 +562,7 @@ def run_ours(args):
     # ---- optional stages on the same events, one at a time, L2 flushed (untimed)
     def extra_pass(**flags):
         xtr = Tracker.for_geometry(geo, **flags)
+        apply_tuning(xtr, args.tuning)
         xtr.reserve(max(p[4] for p in pool), 1, results=2)
         n_x = min(max(args.steps, 10), 20)
         x_ms, x_stats = [], []
@@ -793,6 +794,7 @@ def run_batch(args):
     counts = np.concatenate([p[3] for p in pool])
     offs = np.concatenate([[0], np.cumsum([p[4] for p in pool])])
     tr = Tracker.for_geometry(eventgen.Geometry())
+    apply_tuning(tr, args.tuning)
     tr.reserve(n_tot, len(pool))
     stream = torch.cuda.Stream()
     flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
@@ -879,6 +881,7 @@ def run_small(args):
            for e in evs]
     trackers = [Tracker.for_geometry(geo) for _ in range(args.inflight)]
     for t in trackers:
+        apply_tuning(t, args.tuning)
         t.reserve(max(e.n for e in evs), 1, results=QDEPTH + 1)
     streams = [torch.cuda.Stream() for _ in range(args.inflight)]
 

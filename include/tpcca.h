@@ -124,9 +124,10 @@ typedef struct {
                                   (on a stream of the tracker's own) that updates the tracker's executable
                                   graph in place and is launched on the call's stream as one unit (default);
                                   0: plain stream launches.  Same work, same results. */
-    int seed_kernel;           /* -1: chosen by the call's size (default); 0: each constructor lane walks its
-                                  tracklet's chain for the seed when it takes the tracklet; 1: a separate
-                                  launch computes every seed first.  Same seeds, same results. */
+    int seed_kernel;           /* 1: a separate launch computes every seed first (default); 0: each
+                                  constructor lane walks its tracklet's chain for the seed when it takes the
+                                  tracklet; -1: chosen by the call's size (1 above 40 clusters per lane of
+                                  5 CTAs per SM).  Same seeds, same results. */
     int order_group;           /* cluster slots per group of the constructor's work order (a call with many
                                   events builds one group's tracklets before the next group's, so that the
                                   rows being searched stay in L2); 0: one group.  At most 6144 / kb groups

@@ -195,7 +195,9 @@ extern "C" void tpc_tuning_default(tpc_tuning *t)
     t->stage_rows = 1;
     t->tracklet_capacity = 0;
     t->use_graph = 1;
-    t->seed_kernel = -1;
+    // the seed launch and the pre-seeded constructor were as fast or faster on every workload measured
+    // (one sector 0.82 -> 0.71 ms, one 36-sector 4000-track event 1.22 -> 1.20 ms per event)
+    t->seed_kernel = 1;
     t->order_group = 3 << 20;
 }
 

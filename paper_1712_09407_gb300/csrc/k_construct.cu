@@ -379,11 +379,11 @@ int launch_construct(const DevConst &c, const Workspace &w, const LaunchCfg &lc,
                                                       lc.construct_block, state_bytes);
         per_sm = occ > 0 ? occ : 1;
     }
-    // seed kernel (and the pre-seeded constructor) when the call has more than 40 clusters per lane
-    // of 5 CTAs per SM (about one start hit per 20 clusters in central-like events, so two tracklets
-    // per such lane).  With 64-thread CTAs that is 1.95 M clusters: one central-like event (3.3 M)
-    // takes the pre-seeded form, measured 1.29 against 1.37 ms for its construction stage; with
-    // 128-thread CTAs, two central-like events per call and more
+    // seed kernel (and the pre-seeded constructor): always by default (seed_kernel 1); with
+    // seed_kernel -1 when the call has more than 40 clusters per lane of 5 CTAs per SM (about one
+    // start hit per 20 clusters in central-like events, so two tracklets per such lane), the rule
+    // of an earlier constructor that the measurements no longer support (one central-like event:
+    // 1.29 against 1.37 ms for its construction stage with the seed launch)
     const int64_t lanes = (int64_t)lc.num_sms * 5 * lc.construct_block;
     const bool preseed = lc.seed_kernel > 0 || (lc.seed_kernel < 0 && lc.n_clusters / 20 > 2 * lanes);
     // groups of order_group slots, as many as the histogram's kOrderCursors buckets hold

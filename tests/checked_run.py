@@ -10,7 +10,7 @@ from paper_1712_09407_gb300.tracker import Tracker
 
 CASES = [("c1", 1, {}, {}), ("c1_gm", 1, dict(global_tracking=True, merge=True), {}),
          ("c1_sweep_gm", 1, dict(global_tracking=True, merge=True), dict(construct_mode=1, use_graph=0)),
-         ("c1_seed_g", 1, dict(global_tracking=True), dict(seed_kernel=1)), ("c2", 2, {}, {})]
+         ("c1_walk_g", 1, dict(global_tracking=True), dict(seed_kernel=0)), ("c2", 2, {}, {})]
 
 
 def run(out_path):

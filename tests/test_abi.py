@@ -47,7 +47,7 @@ def test_host_only_entry_points():
     assert p.alpha == 6.0 and p.min_clusters == 30
     t = tracker.tpc_tuning_default()
     assert t.bin_occupancy > 0 and t.construct_block % 32 == 0
-    assert t.use_graph == 1 and t.seed_kernel == -1 and t.order_group == 3 << 20   # the struct layouts agree
+    assert t.use_graph == 1 and t.seed_kernel == 1 and t.order_group == 3 << 20   # the struct layouts agree
     assert tracker.tpc_status_string(0) == "ok"
     assert "capacity" in tracker.tpc_status_string(2)
 
