@@ -361,6 +361,7 @@ def run_reference(args):
 QDEPTH = 16    # calls each tracker has outstanding in the streamed legs (its result ring holds one more): about
               # 120 ms of queued device work over two streams, so that a host pause does not starve the device
 PREROLL_CYCLES = 10_000_000   # about 5 ms at 2 GHz
+E2E_DEPTH = 3                  # calls outstanding per tracker in the end-to-end leg
 STAGES = ["setup", "ingest", "neighbours", "evolution", "construction", "selection", "output", "global", "merge"]
 
 
@@ -701,47 +702,50 @@ def e2e_leg(args, torch, pool, calls, trackers, streams, tr1, stream, flush, B, 
                 times.append(t1 - t0)
     serial_e2e = replica_throughput(reduce_max(sum(times), world, "cuda"), len(times), world)
 
-    # calls in flight, one per tracker
+    # a stream of calls through the trackers, E2E_DEPTH calls outstanding per tracker (the host
+    # submits the next calls, host input and all, while earlier ones compute, and copies each
+    # result back as soon as it is done); timed in the steady state, from the result of one call
+    # to the result of the call n_e2e calls later, so the window holds n_e2e submissions (each with
+    # its host-to-device copy) and n_e2e results copied back
     nf = len(trackers)
-    pend, hb = [None] * nf, [None] * nf
+    hb = [None] * nf
     moved = {"h2d": 0, "d2h": 0}
+    n_warm = 2 * E2E_DEPTH * nf
+    n_e2e = max(args.steps, 40)
+    n_total = n_warm + n_e2e + E2E_DEPTH * nf
+    done_t = {}
+    pend = collections.deque()
 
-    def retire(i, count):
-        r = pend[i]
+    def retire():
+        k, i, r = pend.popleft()
         M, H = r.sync()
         hb[i] = host_bufs(hb[i], M, H)
         tpc_result_copy_to_host(r.handle, hb[i])
         r.release()
-        pend[i] = None
-        if count:
+        done_t[k] = time.perf_counter()
+        if n_warm <= k < n_warm + n_e2e:
             moved["d2h"] += M * (5 + 15 + 3 + 5) * 4 + H * 4 + 48
 
-    def pipelined(n, count):
-        for k in range(n):
-            i = k % nf
-            if pend[i] is not None:
-                retire(i, count)
-            c_ = calls[k % len(calls)]
-            pend[i] = trackers[i].track_batch_host(c_["hy"], c_["hz"], c_["hr"], c_["counts"], B, stream=streams[i])
-            if count:
-                moved["h2d"] += c_["n"] * 9
-        for i in range(nf):
-            if pend[i] is not None:
-                retire(i, count)
-
-    pipelined(max(args.warmup, 2) * nf, False)
-    n_e2e = max(args.steps, 6 * nf)
     torch.cuda.synchronize()
     gc.disable()
-    t0 = time.perf_counter()
-    pipelined(n_e2e, True)
-    wall_e2e = time.perf_counter() - t0
+    for k in range(n_total):
+        if len(pend) >= nf * E2E_DEPTH:
+            retire()
+        i = k % nf
+        c_ = calls[k % len(calls)]
+        pend.append((k, i, trackers[i].track_batch_host(c_["hy"], c_["hz"], c_["hr"], c_["counts"], B, stream=streams[i])))
+        if n_warm <= k < n_warm + n_e2e:
+            moved["h2d"] += c_["n"] * 9
+    while pend:
+        retire()
     gc.enable()
+    wall_e2e = done_t[n_warm + n_e2e - 1] - done_t[n_warm - 1]
     e2e_v = replica_throughput(reduce_max(wall_e2e, world, "cuda"), n_e2e * B, world)
     return {"value": e2e_v, "unit": "events/s", "h2d_bytes_per_step": int(moved["h2d"] / n_e2e),
             "d2h_bytes_per_step": int(moved["d2h"] / n_e2e), "steps": n_e2e, "events_per_step": B,
             "path": "tpc_track_batch_host (pinned host input, %d events per call) + tpc_result_copy_to_host, "
-                    "wall clock, %d calls in flight on %d trackers" % (B, nf, nf),
+                    "wall clock between results %d calls apart in the steady state, %d calls outstanding on "
+                    "each of %d trackers" % (B, n_e2e, E2E_DEPTH, nf),
             "one_event_at_a_time": serial_e2e}
 
 

@@ -254,7 +254,9 @@ int tpc_result_ready(tpc_result *res);
 int tpc_result_get(tpc_result *res, tpc_track_view *view);
 
 /* Copy the whole result to host buffers sized from tpc_result_sync_counts
- * (any pointer may be NULL to skip that array).  Synchronous. */
+ * (any pointer may be NULL to skip that array).  Synchronous: returns when the result's call
+ * has finished and its arrays are in the host buffers.  The copies run on a stream of the
+ * tracker's own, so they do not wait for later calls queued on the call's stream. */
 int tpc_result_copy_to_host(tpc_result *res, float *par, float *cov, float *x_ref, float *alpha,
                             float *chi2, int32_t *ndf, int32_t *nhits, int32_t *first,
                             int32_t *sector, int32_t *event, int32_t *hits);

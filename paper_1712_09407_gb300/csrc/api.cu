@@ -90,6 +90,10 @@ struct tpc_tracker {
     int last_err[4] = {0, 0, 0, 0};
     // graph mode (tuning.use_graph)
     cudaStream_t cap_stream = nullptr;
+    // copies of finished results to the host (tpc_result_copy_to_host): a stream of their own, so
+    // that a copy waits only for its own call and not for the later calls queued on the call's
+    // stream; created at the first copy, freed with the tracker object
+    cudaStream_t copy_stream = nullptr;
     cudaGraphExec_t gexec = nullptr;
     int64_t graph_builds = 0;
     std::mutex mu;
@@ -1046,7 +1050,13 @@ extern "C" int tpc_result_copy_to_host(tpc_result *r, float *par, float *cov, fl
     int s = tpc_result_sync_counts(r, nullptr, nullptr);
     if (s != TPC_OK) return s;
     const int64_t M = r->n_tracks, H = r->n_hits;
-    cudaStream_t st = r->stream;
+    cudaStream_t st;
+    {
+        std::lock_guard<std::mutex> g(r->tr->mu);
+        if (!r->tr->copy_stream) TPC_CUDA(cudaStreamCreateWithFlags(&r->tr->copy_stream, cudaStreamNonBlocking));
+        st = r->tr->copy_stream;
+    }
+    TPC_CUDA(cudaStreamWaitEvent(st, r->done, 0));     // complete already (synced above): orders the copies
     struct Item {
         void *dst;
         const void *src;
@@ -1113,6 +1123,7 @@ static void free_tracker(tpc_tracker *tr)
 {
     for (tpc_result *r : tr->free_results) destroy_result(r);
     tr->free_results.clear();
+    if (tr->copy_stream) cudaStreamDestroy(tr->copy_stream);
     delete tr;
 }
 
