@@ -444,6 +444,7 @@ def run_ours(args):
     from __graft_entry__ import build
     build()
     from paper_1712_09407_gb300 import eventgen
+    from paper_1712_09407_gb300.serving import page_in_mapped_files
     from paper_1712_09407_gb300.tracker import Tracker
 
     # Resident inputs: `resident` different central-like events (together more than the 129 MB L2),
@@ -493,7 +494,9 @@ def run_ours(args):
     sb = Streamer(torch, trackers, streams, world)
     s1 = Streamer(torch, trackers1, streams, world)
     # warm-up: the timed pattern itself (same trackers, streams, call shape and depth of outstanding
-    # calls), so that graphs, staging buffers and result buffers are all in use before timing
+    # calls), so that graphs, staging buffers and result buffers are all in use before timing; the
+    # process's mapped files are read once first, so that no page of them is fetched mid-region
+    page_in_mapped_files()
     n_warm = max(args.warmup, args.inflight * (QDEPTH + 2))
     sb.run(n_warm, call_b, timed=False)
     s1.run(n_warm, call_1, timed=False)
