@@ -24,6 +24,8 @@ from __future__ import annotations
 import collections
 import dataclasses
 import math
+import os
+import stat
 import time
 
 import numpy as np
@@ -380,11 +382,18 @@ def page_in_mapped_files() -> int:
             continue
         seen.add(parts[5])
         try:
+            # regular files only, at most their size: device mappings (the GPU driver's, /dev/zero)
+            # would read without end
+            st = os.stat(parts[5])
+            if not stat.S_ISREG(st.st_mode):
+                continue
+            left = st.st_size
             with open(parts[5], "rb") as f:
-                while True:
-                    b = f.read(1 << 24)
+                while left > 0:
+                    b = f.read(min(left, 1 << 24))
                     if not b:
                         break
+                    left -= len(b)
                     total += len(b)
         except OSError:
             pass
