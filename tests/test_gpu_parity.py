@@ -307,6 +307,58 @@ def test_batch_equals_one_at_a_time():
     tr.close()
 
 
+def _event_slice(b, i, offset):
+    """The tracks of event i of a batch result, with its own hit indices and offsets."""
+    sel = np.nonzero(b["event"] == i)[0]
+    out = {k: v[sel] for k, v in b.items() if k not in ("event", "first", "hits")}
+    hits = [b["hits"][f:f + n] for f, n in zip(b["first"][sel], b["nhits"][sel])]
+    out["hits"] = (np.concatenate(hits) if hits else b["hits"][:0]) - offset
+    out["first"] = np.concatenate([[0], np.cumsum(out["nhits"])[:-1]]).astype(b["first"].dtype) if len(sel) \
+        else b["first"][:0]
+    return out
+
+
+def test_bench_call_shape_matches_oracle_and_single_events():
+    """The bench step's launch configuration at full size: calls of 3 central-like events
+    (tpc_track_batch) on 2 trackers, each on a stream of its own, both in flight at once.  Every
+    event's tracks equal the same event tracked alone, bit for bit, and two of them are compared
+    with the float oracle at the parity thresholds."""
+    evs = [eventgen.config_event(2, event=i) for i in range(6)]
+    geo = evs[0].geometry
+    one = Tracker.for_geometry(geo)
+    singles = [run_gpu(ev, tracker=one, debug=False)[1] for ev in evs]
+    one.close()
+    trs = [Tracker.for_geometry(geo) for _ in range(2)]
+    streams = [torch.cuda.Stream() for _ in range(2)]
+    calls = []
+    for j in range(2):
+        grp = evs[3 * j:3 * j + 3]
+        inp = [torch.from_numpy(np.concatenate([getattr(e, f) for e in grp])).cuda() for f in ("y", "z", "row")]
+        counts = np.concatenate([e.counts for e in grp])
+        torch.cuda.synchronize()                 # inputs copied before the call's stream reads them
+        calls.append((grp, inp, trs[j].track_batch(*inp, counts, 3, stream=streams[j])))
+    for j, (grp, inp, res) in enumerate(calls):
+        res.sync()
+        b = res.to_numpy()
+        res.release()
+        off = 0
+        for i, ev in enumerate(grp):
+            k = 3 * j + i
+            got = _event_slice(b, i, off)
+            for name, v in got.items():
+                assert np.array_equal(v, singles[k][name]), (k, name)
+            if k < 2:
+                ref = run_oracle(ev, key="c2" if k == 0 else "c2_event%d" % k)
+                c = compare_tracks(ev, got, ref)
+                print("bench call shape, event %d: concordance %.7f exact %d/%d" % (
+                    k, c["concordance"], c["n_exact"], c["n_matched"]))
+                assert c["concordance"] >= CONCORDANCE_MIN
+                assert c["par_rel_max"].max() <= PAR_REL
+            off += ev.n
+    for t in trs:
+        t.close()
+
+
 def test_host_input_path_equals_device_path(ev1):
     tr, dev_out, _ = run_gpu(ev1, debug=False)
     res = tr.track_host(ev1.y, ev1.z, ev1.row, ev1.counts)
