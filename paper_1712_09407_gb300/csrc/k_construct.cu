@@ -133,7 +133,7 @@ __global__ void __launch_bounds__(256) k_seed(const DevConst c, const Workspace 
 constexpr int kSearchBatch = 4;   // candidates whose loads a row search issues together
 
 // Where a lane keeps its filter state between row visits (the state at its last fitted cluster):
-// in registers, or in the CTA's shared memory, one column per thread (conflict-free), which frees
+// in registers, or in the CTA's shared memory (21 floats per thread, see StateShared), which frees
 // about 20 registers for more resident warps.  The prediction of a visit is always in registers.
 constexpr bool kStateInShared = true;
 constexpr int kConstructCtasPerSm = kStateInShared ? 6 : 5;
@@ -238,9 +238,11 @@ __device__ __forceinline__ void next_row(const DevConst &c, const Workspace &w, 
     }
 }
 
-// 128 threads and kConstructCtasPerSm resident CTAs per SM.  With the state in shared memory:
-// 80 registers, no spills, 6 CTAs (measured 3 % faster than the state in registers at 96
-// registers and 5 CTAs; 7 or 8 CTAs spill and are slower).
+// Register budget: the bounds of 128 threads and kConstructCtasPerSm CTAs per SM give 80
+// registers with the state in shared memory, no spills (3 % faster than the state in registers at
+// 96 registers and 5 CTAs; 7 or 8 CTAs of 128 spill and are slower).  The same budget admits the
+// default launch, 11 CTAs of 64 threads per SM; 88 registers were slower with two calls on the
+// device at once (no room left for the other call's kernels), and 72 spill.
 // GLOBAL: also store the outward pass's final state (the outer end for global tracking); a
 // separate instance so that the plain tracker keeps its register allocation.
 // PRESEED selects between two shapes of the same loop (same rows, same arithmetic, same results):
